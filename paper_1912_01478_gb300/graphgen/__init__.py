@@ -1,0 +1,215 @@
+"""Seeded synthetic graph generators (inputs only; no colouring arithmetic).
+
+Thin ctypes binding over ``libgraphgen.so`` (built from ``graphgen.c`` beside
+this file by :func:`build`). Every graph is undirected, symmetric, has no
+self-loops or duplicate edges and sorted CSR rows, matching the preprocessing
+the paper applies to its inputs (Section V). Arrays come back as numpy int32
+(rowptr, col) or int64 (batch offsets).
+
+Both the CPU oracle's tests and the GPU path consume these bytes; the graphs
+stand in for the paper's UFL/SuiteSparse inputs (Table I), which are not
+available here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graphgen.c")
+_LIB = os.path.join(_HERE, "libgraphgen.so")
+_lock = threading.Lock()
+_lib = None
+
+# Paper-shaped workload parameters (seeded, synthetic).
+RMAT_ABC = (0.57, 0.19, 0.19)
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("nnz", ctypes.c_int64),
+        ("rowptr", ctypes.POINTER(ctypes.c_int32)),
+        ("col", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+class _Batch(ctypes.Structure):
+    _fields_ = [
+        ("num_graphs", ctypes.c_int32),
+        ("node_off", ctypes.POINTER(ctypes.c_int64)),
+        ("edge_off", ctypes.POINTER(ctypes.c_int64)),
+        ("rowptr_cat", ctypes.POINTER(ctypes.c_int32)),
+        ("col_cat", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile libgraphgen.so with gcc (OpenMP over graphs of a batch)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "graphgen.h"))
+        ):
+            tmp = _LIB + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.POINTER
+    i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    lib.gg_er.argtypes = [u64, i32, i64, P(_Csr)]
+    lib.gg_rmat.argtypes = [u64, i32, i64, dbl, dbl, dbl, i32, i32, P(_Csr)]
+    lib.gg_road.argtypes = [u64, i32, dbl, dbl, P(_Csr)]
+    lib.gg_from_edges.argtypes = [i32, i64, P(i32), P(i32), P(_Csr)]
+    lib.gg_batch.argtypes = [u64, i32, i32, i32, dbl, dbl, i32, dbl, dbl, dbl, P(_Batch)]
+    lib.gg_free_csr.argtypes = [P(_Csr)]
+    lib.gg_free_batch.argtypes = [P(_Batch)]
+    lib.gg_hash_words.argtypes = [P(i32), i64, u64]
+    lib.gg_hash_words.restype = u64
+    lib.gg_derive_seed.argtypes = [u64, u64]
+    lib.gg_derive_seed.restype = u64
+    lib.gg_num_threads.restype = ctypes.c_int
+    for f in (lib.gg_er, lib.gg_rmat, lib.gg_road, lib.gg_from_edges, lib.gg_batch):
+        f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _take(c: _Csr):
+    lib = _load()
+    n, nnz = int(c.n), int(c.nnz)
+    rowptr = np.ctypeslib.as_array(c.rowptr, shape=(n + 1,)).copy()
+    col = (
+        np.ctypeslib.as_array(c.col, shape=(nnz,)).copy() if nnz > 0 else np.zeros(0, np.int32)
+    )
+    lib.gg_free_csr(ctypes.byref(c))
+    return rowptr, col
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"graphgen {what} failed with code {rc}")
+
+
+def er(n: int, m: int, seed: int):
+    """Erdos-Renyi G(n, m) with exactly m undirected edges. Returns (rowptr, col)."""
+    c = _Csr()
+    _check(_load().gg_er(seed, n, m, ctypes.byref(c)), "er")
+    return _take(c)
+
+
+def rmat(scale: int, edge_factor: int, seed: int, abc=RMAT_ABC, n_limit: int = 0, permute=True):
+    """RMAT with edge_factor * 2^scale directed draws, symmetrised, IDs permuted."""
+    a, b, cc = abc
+    c = _Csr()
+    nedges = int(edge_factor) * (n_limit if n_limit > 0 else (1 << scale))
+    _check(
+        _load().gg_rmat(seed, scale, nedges, a, b, cc, n_limit, 1 if permute else 0, ctypes.byref(c)),
+        "rmat",
+    )
+    return _take(c)
+
+
+def road(side: int, seed: int, p_delete: float = 0.30, frac_long: float = 0.01):
+    """side x side grid, p_delete of edges removed, frac_long long-range edges added."""
+    c = _Csr()
+    _check(_load().gg_road(seed, side, p_delete, frac_long, ctypes.byref(c)), "road")
+    return _take(c)
+
+
+def from_edges(n: int, src, dst):
+    """CSR (symmetrised, deduplicated, self-loops dropped, rows sorted) from pairs."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    assert src.shape == dst.shape
+    c = _Csr()
+    P = ctypes.POINTER(ctypes.c_int32)
+    _check(
+        _load().gg_from_edges(
+            n, src.size, src.ctypes.data_as(P), dst.ctypes.data_as(P), ctypes.byref(c)
+        ),
+        "from_edges",
+    )
+    return _take(c)
+
+
+def batch(
+    num_graphs: int,
+    seed: int,
+    nmin: int = 100,
+    nmax: int = 200_000,
+    deg_lo: float = 4.0,
+    deg_hi: float = 32.0,
+    rmat_ef: int = 8,
+    abc=RMAT_ABC,
+):
+    """Concatenated batch: dict(node_off, edge_off, rowptr_cat, col_cat)."""
+    b = _Batch()
+    a, bb, c = abc
+    lib = _load()
+    _check(
+        lib.gg_batch(seed, num_graphs, nmin, nmax, deg_lo, deg_hi, rmat_ef, a, bb, c, ctypes.byref(b)),
+        "batch",
+    )
+    G = int(b.num_graphs)
+    node_off = np.ctypeslib.as_array(b.node_off, shape=(G + 1,)).copy()
+    edge_off = np.ctypeslib.as_array(b.edge_off, shape=(G + 1,)).copy()
+    nrp = int(node_off[-1]) + G
+    ncol = int(edge_off[-1])
+    rowptr_cat = np.ctypeslib.as_array(b.rowptr_cat, shape=(nrp,)).copy()
+    col_cat = (
+        np.ctypeslib.as_array(b.col_cat, shape=(ncol,)).copy() if ncol > 0 else np.zeros(0, np.int32)
+    )
+    lib.gg_free_batch(ctypes.byref(b))
+    return dict(node_off=node_off, edge_off=edge_off, rowptr_cat=rowptr_cat, col_cat=col_cat)
+
+
+def batch_graph(bt: dict, g: int):
+    """(rowptr, col) views of graph g inside a batch dict."""
+    no, eo = bt["node_off"], bt["edge_off"]
+    n = int(no[g + 1] - no[g])
+    rp = bt["rowptr_cat"][int(no[g]) + g : int(no[g]) + g + n + 1]
+    cl = bt["col_cat"][int(eo[g]) : int(eo[g + 1])]
+    return rp, cl
+
+
+def graph_hash(rowptr, col) -> int:
+    """FNV-1a 64 over rowptr then col (little-endian int32 words)."""
+    lib = _load()
+    P = ctypes.POINTER(ctypes.c_int32)
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    h = lib.gg_hash_words(rp.ctypes.data_as(P), rp.size, 0)
+    return int(lib.gg_hash_words(cl.ctypes.data_as(P), cl.size, h))
+
+
+def derive_seed(seed: int, index: int) -> int:
+    return int(_load().gg_derive_seed(seed, index))
+
+
+def num_threads() -> int:
+    return int(_load().gg_num_threads())
+
+
+# Named workloads: the paper-shaped synthetic inputs (sizes as stated).
+def workload(name: str):
+    """Return (rowptr, col) for a named single-graph workload."""
+    if name == "er_n10000_deg8_seed1":
+        return er(10_000, 40_000, seed=1)
+    if name == "rmat_s22_ef16_seed2":
+        return rmat(22, 16, seed=2)
+    if name == "road_4096_seed3":
+        return road(4096, seed=3)
+    raise KeyError(name)
