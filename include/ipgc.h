@@ -1,0 +1,197 @@
+/*
+ * ipgc.h -- C ABI of libipgc.so: hybrid IPGC graph colouring on one GB300.
+ *
+ * The library colours an undirected graph with the Iterative Parallel Graph
+ * Coloring (IPGC) loop of "A Hybrid Graph Coloring Algorithm for GPUs"
+ * (Section II-C): every uncoloured node takes the smallest colour not used by
+ * its neighbours (first fit, the footnote's mex), conflicting endpoints are
+ * uncoloured again, and the loop repeats until the worklist of uncoloured
+ * nodes is empty. Each iteration runs either topology-driven (sweep every
+ * node) or data-driven (sweep the worklist), chosen from the worklist size
+ * (Section IV, threshold H, about 60 % of the node count); the worklist is
+ * kept up to date in every iteration, in both modes (Sections I and IV).
+ *
+ * Result semantics (fixed, deterministic; the same for every mode, driver and
+ * entry point):
+ *   - colour 0 means "uncoloured"; valid colours are 1, 2, ...;
+ *   - tentative colours are taken from the snapshot of committed colours at
+ *     the start of the round (active neighbours count as uncoloured);
+ *   - of two adjacent active nodes with the same tentative colour the one
+ *     with the higher node ID loses and stays in the worklist;
+ *   - one round = one assignment step + one conflict step; the last,
+ *     conflict-free round is counted; num_colors = the largest colour.
+ *
+ * Graph input: CSR with int32 rowptr[n + 1] and int32 col[nnz] (directed
+ * entries, both directions of every undirected edge), no self-loops, no
+ * duplicate entries, every row sorted ascending (the paper removes self
+ * loops and multi-edges before colouring, Section V). nnz < 2^31.
+ *
+ * Conventions for every entry point:
+ *   - returns IPGC_OK (0), IPGC_PENDING (1) or a negative IPGC_ERR_* code;
+ *     never aborts, never prints, never throws across the ABI;
+ *   - "device pointer" arguments are CUDA device memory on the context's
+ *     device, owned by the caller, which must stay valid until the call has
+ *     completed on its stream; "host pointer" arguments are plain host memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream);
+ *   - the library allocates only its own workspace, held in the context and
+ *     released by ipgc_ctx_destroy.
+ */
+#ifndef IPGC_H
+#define IPGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IPGC_API __attribute__((visibility("default")))
+#else
+#define IPGC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IPGC_OK 0
+#define IPGC_PENDING 1
+#define IPGC_ERR_INVALID (-1)     /* bad argument or CSR (see ipgc_validate_csr) */
+#define IPGC_ERR_OOM (-2)         /* device or host allocation failed */
+#define IPGC_ERR_TIMEOUT (-3)     /* a bounded device-side wait expired */
+#define IPGC_ERR_NO_CONVERGE (-4) /* more than max_rounds rounds */
+#define IPGC_ERR_CUDA (-5)        /* a CUDA call failed; see ipgc_ctx_cuda_error */
+#define IPGC_ERR_BUSY (-6)        /* server: request not admissible right now */
+#define IPGC_ERR_UNSUPPORTED (-7) /* option combination not available */
+#define IPGC_ERR_NOT_FOUND (-8)   /* server: unknown ticket */
+
+/* Mode policy: how each round chooses topology- or data-driven work. */
+#define IPGC_MODE_THRESHOLD 0 /* topology iff |WL| > floor(threshold_frac * n) (Section IV) */
+#define IPGC_MODE_TOPO 1      /* every round topology-driven (still pushes the worklist) */
+#define IPGC_MODE_DATA 2      /* every round data-driven ("Plain" IPGC, Section II-C) */
+#define IPGC_MODE_LEARNED 3   /* per-round MLP loaded by ipgc_policy_load; threshold fallback */
+
+/* Driver: where the round loop runs (the paper's Iteration Outlining, Section V). */
+#define IPGC_DRIVER_PERSISTENT 0 /* one cooperative launch, rounds separated by grid barriers */
+#define IPGC_DRIVER_HOSTLOOP 1   /* one launch per phase, host reads |WL| after every round */
+
+typedef struct ipgc_ctx ipgc_ctx;
+
+typedef struct ipgc_stats {
+  int32_t rounds;          /* rounds executed */
+  int32_t num_colors;      /* largest colour = number of distinct colours */
+  int32_t rounds_topo;     /* rounds run topology-driven */
+  int32_t rounds_data;     /* rounds run data-driven */
+  int64_t edges_processed; /* sum over rounds of the degrees of the active nodes */
+  uint64_t ns;             /* device time of the colouring loop (%globaltimer) */
+  int32_t error;           /* IPGC_OK or the error the device reported */
+  int32_t reserved;
+} ipgc_stats;
+
+/* One record per round, written to ipgc_options.trace when it is non-NULL. */
+typedef struct ipgc_trace_rec {
+  int32_t round;      /* 1-based */
+  int32_t mode;       /* IPGC_MODE_TOPO or IPGC_MODE_DATA: how this round ran */
+  int64_t wl_size;    /* |WL| at the start of the round */
+  int64_t deg_sum;    /* sum of deg(v) over the worklist */
+  int32_t max_color;  /* largest committed colour at the start of the round */
+  int32_t shortcut;   /* 1 for round 1, whose assignment step is implicit */
+  uint64_t t_begin;   /* %globaltimer at the start of the round (ns) */
+  uint64_t t_assign;  /* ... after the assignment step's grid barrier */
+  uint64_t t_detect;  /* ... after the conflict step's grid barrier */
+} ipgc_trace_rec;
+
+typedef struct ipgc_options {
+  int32_t mode;           /* IPGC_MODE_*; default THRESHOLD */
+  float threshold_frac;   /* H = floor(threshold_frac * n); default 0.6 (Section IV) */
+  int32_t driver;         /* IPGC_DRIVER_*; default PERSISTENT */
+  int32_t max_rounds;     /* 0 = n + 1, which always suffices */
+  uint64_t timeout_ns;    /* limit for each device-side wait; 0 = 10 s */
+  int32_t validate;       /* 1 = check the CSR on the device first (IPGC_ERR_INVALID) */
+  int32_t t1;             /* degree <= t1: a warp handles 32 such nodes together; 0 = default */
+  int32_t t2;             /* t1 < degree <= t2: one warp per node; above: one CTA; 0 = default */
+  int32_t block_size;     /* threads per CTA of the colouring kernel; 0 = default */
+  int32_t blocks_per_sm;  /* resident CTAs per SM; 0 = as many as fit */
+  ipgc_trace_rec* trace;  /* device pointer to trace_cap records, or NULL */
+  int32_t* fin_round;     /* device pointer to int32[n] receiving the round in which each
+                             node's colour was committed, or NULL */
+  int32_t trace_cap;
+  int32_t fault_inject;   /* tests only: 1 = every grid barrier also waits for a CTA that
+                             never arrives, so the launch ends with IPGC_ERR_TIMEOUT after
+                             timeout_ns (exercises the bounded waits); 0 otherwise */
+} ipgc_options;
+
+/* Fill *opt with the defaults listed above. */
+IPGC_API void ipgc_options_default(ipgc_options* opt);
+
+/* Message for a status code (static storage, never NULL). */
+IPGC_API const char* ipgc_strerror(int status);
+
+/*
+ * Create a context on CUDA device `device`. The context owns the workspace
+ * (tentative colours, worklists, control block), grown on demand and reused
+ * by later calls. A context must not be used by two host threads at once.
+ * Errors: IPGC_ERR_INVALID (bad device), IPGC_ERR_CUDA, IPGC_ERR_OOM.
+ */
+IPGC_API int ipgc_ctx_create(ipgc_ctx** out, int device);
+IPGC_API int ipgc_ctx_destroy(ipgc_ctx* ctx);
+/* The last CUDA error code (cudaError_t) seen by the context, 0 if none. */
+IPGC_API int ipgc_ctx_cuda_error(const ipgc_ctx* ctx);
+
+/*
+ * Bytes of device workspace a colouring of a graph with n nodes needs
+ * (ipgc_color_ex grows the context's workspace to this size when needed).
+ */
+IPGC_API size_t ipgc_workspace_size(int32_t n);
+
+/*
+ * Colour one graph (Section II-C's loop with Section IV's hybrid schedule).
+ *   rowptr      device pointer, int32[n + 1], rowptr[0] = 0, rowptr[n] = nnz
+ *   col         device pointer, int32[nnz], see "Graph input" above
+ *   n, nnz      node and entry counts (n >= 0, 0 <= nnz < 2^31)
+ *   colors_out  device pointer, int32[n]; receives colours 1..num_colors
+ *   stats_out   host pointer or NULL. Non-NULL: the call waits for the stream
+ *               and fills the statistics (device-side errors are returned).
+ *               NULL: the call only enqueues work and returns IPGC_OK; read
+ *               the outcome with ipgc_ctx_last_stats after synchronising.
+ *   opt         host pointer or NULL (defaults)
+ *   stream      cudaStream_t or NULL
+ * ipgc_color is ipgc_color_ex on a per-thread default context for the current
+ * device, default options and the legacy default stream.
+ * Errors: IPGC_ERR_INVALID (arguments; CSR if opt->validate), IPGC_ERR_OOM,
+ * IPGC_ERR_TIMEOUT, IPGC_ERR_NO_CONVERGE, IPGC_ERR_CUDA.
+ */
+IPGC_API int ipgc_color(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+               int32_t* colors_out, ipgc_stats* stats_out);
+IPGC_API int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+                  int32_t* colors_out, ipgc_stats* stats_out, const ipgc_options* opt,
+                  void* stream);
+
+/* Statistics of the context's last colouring; waits for its stream. */
+IPGC_API int ipgc_ctx_last_stats(ipgc_ctx* ctx, ipgc_stats* stats_out);
+
+/*
+ * As ipgc_color_ex, but rowptr, col and colors_out are HOST pointers: the
+ * call copies the graph to device buffers held by the context, colours it and
+ * copies the colours back, all on `stream`, and returns when they are in
+ * colors_out. Pinned host memory makes the copies faster but is not required.
+ */
+IPGC_API int ipgc_color_host(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
+                    int64_t nnz, int32_t* colors_out, ipgc_stats* stats_out,
+                    const ipgc_options* opt, void* stream);
+
+/*
+ * Check a CSR graph: rowptr[0] == 0, rowptr non-decreasing, rowptr[n] == nnz,
+ * every col entry in [0, n), no self-loop, rows strictly ascending (sorted,
+ * no duplicates) and symmetric (u in row v iff v in row u).
+ * on_device = 1: rowptr/col are device pointers and a kernel checks them on
+ * the context's stream (ctx may be NULL: current device, default stream);
+ * on_device = 0: host pointers, checked on the host. Returns IPGC_OK or
+ * IPGC_ERR_INVALID.
+ */
+IPGC_API int ipgc_validate_csr(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
+                      int64_t nnz, int on_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPGC_H */

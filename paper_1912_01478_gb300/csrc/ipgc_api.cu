@@ -1,0 +1,447 @@
+// C ABI of libipgc.so: contexts, workspace, argument checks, drivers.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ipgc_internal.h"
+
+using ipgc::Ctrl;
+using ipgc::Params;
+
+struct ipgc_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int occ_persistent = 0;  // resident CTAs per SM of the persistent kernel
+  // workspace for one colouring: tent, worklists, static lists
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  Ctrl* d_ctrl = nullptr;
+  Ctrl* h_ctrl = nullptr;  // pinned
+  int* d_err = nullptr;
+  int* h_err = nullptr;  // pinned
+  // device copies for ipgc_color_host
+  int32_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  int32_t* d_colors = nullptr;
+  size_t cap_rowptr = 0, cap_col = 0, cap_colors = 0;
+  // learned policy weights
+  float* d_mlp = nullptr;
+  int32_t mlp_len = 0;
+  // state of the last colouring
+  int last_cuda = 0;
+  cudaStream_t last_stream = nullptr;
+  int last_status = IPGC_OK;
+  int last_valid = 0;  // h_ctrl holds a finished colouring
+  int last_trivial = 0;  // n == 0
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
+  if (ctx) ctx->last_cuda = (int)e;
+  return e == cudaErrorMemoryAllocation ? IPGC_ERR_OOM : IPGC_ERR_CUDA;
+}
+
+#define IPGC_CUDA(ctx, call)                      \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
+  } while (0)
+
+// Workspace: tent[n], worklists [2 parities][3 buckets][n], static lists
+// [mid][n] and [big][n], each 256-byte aligned.
+constexpr int kWsArrays = 1 + 2 * ipgc::NB + 2;
+
+size_t ws_bytes_for(int32_t n) { return (size_t)kWsArrays * align256((size_t)n * sizeof(int32_t)); }
+
+int ensure_ws(ipgc_ctx* ctx, int32_t n) {
+  const size_t need = ws_bytes_for(n);
+  if (ctx->ws_bytes >= need && ctx->ws) return IPGC_OK;
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  IPGC_CUDA(ctx, cudaMalloc((void**)&ctx->ws, need));
+  ctx->ws_bytes = need;
+  return IPGC_OK;
+}
+
+template <class T>
+int ensure_buf(ipgc_ctx* ctx, T** p, size_t* cap, size_t count) {
+  if (*cap >= count && *p) return IPGC_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  IPGC_CUDA(ctx, cudaMalloc((void**)p, (count > 0 ? count : 1) * sizeof(T)));
+  *cap = count;
+  return IPGC_OK;
+}
+
+void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t* col, int32_t n,
+                 int64_t nnz, int32_t* colors, const ipgc_options& o) {
+  std::memset(&p, 0, sizeof(p));
+  p.rowptr = rowptr;
+  p.col = col;
+  p.n = n;
+  p.nnz = nnz;
+  p.color = colors;
+  const size_t a = align256((size_t)n * sizeof(int32_t));
+  char* w = ctx->ws;
+  p.tent = (int32_t*)w;
+  w += a;
+  for (int par = 0; par < 2; ++par)
+    for (int b = 0; b < ipgc::NB; ++b) {
+      p.wl[par][b] = (int32_t*)w;
+      w += a;
+    }
+  p.stat[ipgc::B_SMALL] = nullptr;
+  p.stat[ipgc::B_MID] = (int32_t*)w;
+  w += a;
+  p.stat[ipgc::B_BIG] = (int32_t*)w;
+  p.ctrl = ctx->d_ctrl;
+  p.trace = o.trace;
+  p.fin = o.fin_round;
+  p.trace_cap = o.trace ? o.trace_cap : 0;
+  p.t1 = o.t1 > 0 ? (o.t1 < ipgc::kMaxT1 ? o.t1 : ipgc::kMaxT1) : ipgc::kDefaultT1;
+  p.t2 = o.t2 > 0 ? (o.t2 < ipgc::kMaxT2 ? o.t2 : ipgc::kMaxT2) : ipgc::kDefaultT2;
+  if (p.t2 < p.t1) p.t2 = p.t1;
+  double h = (double)o.threshold_frac * (double)n;
+  if (h < 0) h = 0;
+  p.H = (int64_t)h;  // floor for h >= 0
+  p.policy = o.mode;
+  p.max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : INT32_MAX);
+  p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
+  p.mlp = (o.mode == IPGC_MODE_LEARNED) ? ctx->d_mlp : nullptr;
+  p.bar_extra = o.fault_inject ? 1u : 0u;
+}
+
+void stats_from_ctrl(const Ctrl& c, ipgc_stats* st) {
+  st->rounds = c.rounds;
+  st->num_colors = c.maxc;
+  st->rounds_topo = c.rounds_topo;
+  st->rounds_data = c.rounds_data;
+  st->edges_processed = (int64_t)c.edges;
+  st->ns = c.t_end >= c.t_start ? c.t_end - c.t_start : 0;
+  st->error = c.status;
+  st->reserved = 0;
+}
+
+int check_graph_args(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+                     const int32_t* colors) {
+  if (n < 0 || nnz < 0 || nnz > (int64_t)INT32_MAX) return IPGC_ERR_INVALID;
+  if (n > 0 && (!rowptr || !colors)) return IPGC_ERR_INVALID;
+  if (nnz > 0 && (!col || n == 0)) return IPGC_ERR_INVALID;
+  if (n == INT32_MAX) return IPGC_ERR_INVALID;
+  return IPGC_OK;
+}
+
+int run_validate(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+                 cudaStream_t s) {
+  IPGC_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+  int blocks = ctx->num_sms * 8;
+  IPGC_CUDA(ctx, ipgc::launch_validate(rowptr, col, n, nnz, ctx->d_err, blocks, s));
+  IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  IPGC_CUDA(ctx, cudaStreamSynchronize(s));
+  return *ctx->h_err ? IPGC_ERR_INVALID : IPGC_OK;
+}
+
+int run_hostloop(ipgc_ctx* ctx, const Params& p, int blocks, cudaStream_t s) {
+  IPGC_CUDA(ctx, ipgc::launch_round1(p, blocks, s));
+  int r = 2;
+  for (;; ++r) {
+    IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctrl, ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    IPGC_CUDA(ctx, cudaStreamSynchronize(s));
+    const int par = r & 1;
+    const int64_t total =
+        (int64_t)ctx->h_ctrl->cnt[par][0] + ctx->h_ctrl->cnt[par][1] + ctx->h_ctrl->cnt[par][2];
+    if (total == 0) break;
+    if (r > p.max_rounds) {
+      ctx->h_ctrl->status = IPGC_ERR_NO_CONVERGE;
+      IPGC_CUDA(ctx, cudaMemcpyAsync(&ctx->d_ctrl->status, &ctx->h_ctrl->status, sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, s));
+      break;
+    }
+    int mode;
+    if (p.policy == IPGC_MODE_TOPO)
+      mode = IPGC_MODE_TOPO;
+    else if (p.policy == IPGC_MODE_DATA)
+      mode = IPGC_MODE_DATA;
+    else
+      mode = total > p.H ? IPGC_MODE_TOPO : IPGC_MODE_DATA;
+    IPGC_CUDA(ctx, ipgc::launch_assign(p, blocks, r, mode, s));
+    IPGC_CUDA(ctx, ipgc::launch_detect(p, blocks, r, mode, s));
+  }
+  IPGC_CUDA(ctx, ipgc::launch_finish(p, r - 1, s));
+  return IPGC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipgc_options_default(ipgc_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = IPGC_MODE_THRESHOLD;
+  o->threshold_frac = 0.6f;
+  o->driver = IPGC_DRIVER_PERSISTENT;
+  o->max_rounds = 0;
+  o->timeout_ns = 0;
+  o->validate = 1;
+}
+
+const char* ipgc_strerror(int s) {
+  switch (s) {
+    case IPGC_OK: return "ok";
+    case IPGC_PENDING: return "pending";
+    case IPGC_ERR_INVALID: return "invalid argument or graph";
+    case IPGC_ERR_OOM: return "out of memory";
+    case IPGC_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+    case IPGC_ERR_NO_CONVERGE: return "did not converge within max_rounds";
+    case IPGC_ERR_CUDA: return "CUDA error (see ipgc_ctx_cuda_error)";
+    case IPGC_ERR_BUSY: return "not admissible now (busy)";
+    case IPGC_ERR_UNSUPPORTED: return "unsupported option";
+    case IPGC_ERR_NOT_FOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+size_t ipgc_workspace_size(int32_t n) { return n > 0 ? ws_bytes_for(n) + align256(sizeof(Ctrl)) : 0; }
+
+int ipgc_ctx_create(ipgc_ctx** out, int device) {
+  if (!out) return IPGC_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return IPGC_ERR_INVALID;
+  ipgc_ctx* ctx = new (std::nothrow) ipgc_ctx();
+  if (!ctx) return IPGC_ERR_OOM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  int rc = IPGC_OK;
+  int coop = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+  if (e == cudaSuccess) e = ipgc::occupancy_persistent(&ctx->occ_persistent);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ctrl, sizeof(Ctrl));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_ctrl, sizeof(Ctrl));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_err, sizeof(int));
+  if (e != cudaSuccess) rc = cuda_fail(ctx, e);
+  if (rc == IPGC_OK && (!coop || ctx->occ_persistent < 1)) rc = IPGC_ERR_UNSUPPORTED;
+  if (rc != IPGC_OK) {
+    ipgc_ctx_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return IPGC_OK;
+}
+
+int ipgc_ctx_destroy(ipgc_ctx* ctx) {
+  if (!ctx) return IPGC_OK;
+  {
+    DeviceGuard g(ctx->device);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_ctrl) cudaFree(ctx->d_ctrl);
+    if (ctx->h_ctrl) cudaFreeHost(ctx->h_ctrl);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    if (ctx->d_rowptr) cudaFree(ctx->d_rowptr);
+    if (ctx->d_col) cudaFree(ctx->d_col);
+    if (ctx->d_colors) cudaFree(ctx->d_colors);
+    if (ctx->d_mlp) cudaFree(ctx->d_mlp);
+  }
+  delete ctx;
+  return IPGC_OK;
+}
+
+int ipgc_ctx_cuda_error(const ipgc_ctx* ctx) { return ctx ? ctx->last_cuda : 0; }
+
+int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+                  int32_t* colors_out, ipgc_stats* stats_out, const ipgc_options* opt,
+                  void* stream) {
+  if (!ctx) return IPGC_ERR_INVALID;
+  int rc = check_graph_args(rowptr, col, n, nnz, colors_out);
+  if (rc != IPGC_OK) return rc;
+  ipgc_options o;
+  if (opt)
+    o = *opt;
+  else
+    ipgc_options_default(&o);
+  if (o.mode < IPGC_MODE_THRESHOLD || o.mode > IPGC_MODE_LEARNED) return IPGC_ERR_INVALID;
+  if (o.driver != IPGC_DRIVER_PERSISTENT && o.driver != IPGC_DRIVER_HOSTLOOP) return IPGC_ERR_INVALID;
+  if (o.block_size != 0 && o.block_size != ipgc::kBlock) return IPGC_ERR_UNSUPPORTED;
+  if (o.trace && o.trace_cap < 0) return IPGC_ERR_INVALID;
+  if (!(o.threshold_frac >= 0.0f)) return IPGC_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+  ctx->last_valid = 0;
+  ctx->last_stream = s;
+  ctx->last_status = IPGC_OK;
+  if (n == 0) {
+    ctx->last_trivial = 1;
+    ctx->last_valid = 1;
+    if (stats_out) std::memset(stats_out, 0, sizeof(*stats_out));
+    return IPGC_OK;
+  }
+  ctx->last_trivial = 0;
+  rc = ensure_ws(ctx, n);
+  if (rc != IPGC_OK) return rc;
+  if (o.validate) {
+    rc = run_validate(ctx, rowptr, col, n, nnz, s);
+    if (rc != IPGC_OK) return rc;
+  }
+  Params p;
+  fill_params(ctx, p, rowptr, col, n, nnz, colors_out, o);
+  IPGC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctrl, 0, sizeof(Ctrl), s));
+  int bps = ctx->occ_persistent;
+  if (o.blocks_per_sm > 0 && o.blocks_per_sm < bps) bps = o.blocks_per_sm;
+  const int blocks = bps * ctx->num_sms;
+  if (o.driver == IPGC_DRIVER_PERSISTENT) {
+    IPGC_CUDA(ctx, ipgc::launch_persistent(p, blocks, s));
+  } else {
+    rc = run_hostloop(ctx, p, blocks, s);
+    if (rc != IPGC_OK) return rc;
+  }
+  IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctrl, ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  ctx->last_valid = 1;
+  if (!stats_out) return IPGC_OK;
+  return ipgc_ctx_last_stats(ctx, stats_out);
+}
+
+int ipgc_ctx_last_stats(ipgc_ctx* ctx, ipgc_stats* st) {
+  if (!ctx || !st) return IPGC_ERR_INVALID;
+  if (!ctx->last_valid) return IPGC_ERR_INVALID;
+  if (ctx->last_trivial) {
+    std::memset(st, 0, sizeof(*st));
+    return IPGC_OK;
+  }
+  DeviceGuard g(ctx->device);
+  IPGC_CUDA(ctx, cudaStreamSynchronize(ctx->last_stream));
+  stats_from_ctrl(*ctx->h_ctrl, st);
+  return st->error;
+}
+
+namespace {
+struct DefaultCtxs {
+  std::vector<ipgc_ctx*> by_dev;
+  ~DefaultCtxs() {
+    for (ipgc_ctx* c : by_dev)
+      if (c) ipgc_ctx_destroy(c);
+  }
+};
+thread_local DefaultCtxs t_default;
+}  // namespace
+
+int ipgc_color(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+               int32_t* colors_out, ipgc_stats* stats_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IPGC_ERR_CUDA;
+  if ((int)t_default.by_dev.size() <= dev) t_default.by_dev.resize(dev + 1, nullptr);
+  if (!t_default.by_dev[dev]) {
+    int rc = ipgc_ctx_create(&t_default.by_dev[dev], dev);
+    if (rc != IPGC_OK) return rc;
+  }
+  ipgc_stats local;
+  return ipgc_color_ex(t_default.by_dev[dev], rowptr, col, n, nnz, colors_out,
+                       stats_out ? stats_out : &local, nullptr, nullptr);
+}
+
+int ipgc_color_host(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
+                    int64_t nnz, int32_t* colors_out, ipgc_stats* stats_out,
+                    const ipgc_options* opt, void* stream) {
+  if (!ctx) return IPGC_ERR_INVALID;
+  int rc = check_graph_args(rowptr, col, n, nnz, colors_out);
+  if (rc != IPGC_OK) return rc;
+  if (n == 0) {
+    if (stats_out) std::memset(stats_out, 0, sizeof(*stats_out));
+    return IPGC_OK;
+  }
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = ensure_buf(ctx, &ctx->d_rowptr, &ctx->cap_rowptr, (size_t)n + 1);
+  if (rc == IPGC_OK) rc = ensure_buf(ctx, &ctx->d_col, &ctx->cap_col, (size_t)nnz);
+  if (rc == IPGC_OK) rc = ensure_buf(ctx, &ctx->d_colors, &ctx->cap_colors, (size_t)n);
+  if (rc != IPGC_OK) return rc;
+  IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->d_rowptr, rowptr, ((size_t)n + 1) * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s));
+  if (nnz > 0)
+    IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->d_col, col, (size_t)nnz * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, s));
+  ipgc_stats local;
+  ipgc_stats* st = stats_out ? stats_out : &local;
+  rc = ipgc_color_ex(ctx, ctx->d_rowptr, ctx->d_col, n, nnz, ctx->d_colors, st, opt, stream);
+  if (rc != IPGC_OK) return rc;
+  IPGC_CUDA(ctx, cudaMemcpyAsync(colors_out, ctx->d_colors, (size_t)n * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s));
+  IPGC_CUDA(ctx, cudaStreamSynchronize(s));
+  return IPGC_OK;
+}
+
+int ipgc_validate_csr(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
+                      int64_t nnz, int on_device, void* stream) {
+  if (n < 0 || nnz < 0 || nnz > (int64_t)INT32_MAX || n == INT32_MAX) return IPGC_ERR_INVALID;
+  if (!rowptr) return IPGC_ERR_INVALID;
+  if (nnz > 0 && !col) return IPGC_ERR_INVALID;
+  if (!on_device) {
+    if (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz) return IPGC_ERR_INVALID;
+    for (int32_t v = 0; v < n; ++v) {
+      const int32_t s = rowptr[v], e = rowptr[v + 1];
+      if (s < 0 || e < s || (int64_t)e > nnz) return IPGC_ERR_INVALID;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+      for (int32_t k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+        const int32_t u = col[k];
+        if (u < 0 || u >= n || u == v) return IPGC_ERR_INVALID;
+        if (k > rowptr[v] && col[k - 1] >= u) return IPGC_ERR_INVALID;
+        int32_t lo = rowptr[u], hi = rowptr[u + 1];
+        const int32_t hi0 = hi;
+        while (lo < hi) {
+          const int32_t mid = lo + ((hi - lo) >> 1);
+          if (col[mid] < v)
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        if (lo >= hi0 || col[lo] != v) return IPGC_ERR_INVALID;
+      }
+    }
+    return IPGC_OK;
+  }
+  if (n == 0) return IPGC_OK;
+  bool own = false;
+  if (!ctx) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return IPGC_ERR_CUDA;
+    int rc = ipgc_ctx_create(&ctx, dev);
+    if (rc != IPGC_OK) return rc;
+    own = true;
+  }
+  int rc;
+  {
+    DeviceGuard g(ctx->device);
+    rc = run_validate(ctx, rowptr, col, n, nnz, (cudaStream_t)stream);
+  }
+  if (own) ipgc_ctx_destroy(ctx);
+  return rc;
+}
+
+}  // extern "C"
