@@ -343,7 +343,7 @@ def main():
             "peak_source": src,
             "algorithmic_bytes_per_launch": int(alg_bytes),
             "avg_launch_ms": avg_launch_s * 1e3,
-            "kernel": "persistent_kernel<512>",
+            "kernel": "persistent_kernel<256>",
         },
         "e2e": {
             "value": e2e_val,

@@ -107,8 +107,10 @@ typedef struct ipgc_options {
   int32_t max_rounds;     /* 0 = n + 1, which always suffices */
   uint64_t timeout_ns;    /* limit for each device-side wait; 0 = 10 s */
   int32_t validate;       /* 1 = check the CSR on the device first (IPGC_ERR_INVALID) */
-  int32_t t1;             /* degree <= t1: a warp handles 32 such nodes together; 0 = default */
-  int32_t t2;             /* t1 < degree <= t2: one warp per node; above: one CTA; 0 = default */
+  int32_t t1;             /* degree <= t1 (<= 63): a warp colours 32 such nodes together;
+                             0 = default 24 */
+  int32_t chunk;          /* degree > t1: the node's neighbours are cut into work items of
+                             this many (32..4096), one warp each; 0 = default 1024 */
   int32_t block_size;     /* threads per CTA of the colouring kernel; 0 = default */
   int32_t blocks_per_sm;  /* resident CTAs per SM; 0 = as many as fit */
   ipgc_trace_rec* trace;  /* device pointer to trace_cap records, or NULL */
@@ -138,10 +140,11 @@ IPGC_API int ipgc_ctx_destroy(ipgc_ctx* ctx);
 IPGC_API int ipgc_ctx_cuda_error(const ipgc_ctx* ctx);
 
 /*
- * Bytes of device workspace a colouring of a graph with n nodes needs
+ * Bytes of device workspace a colouring of a graph with n nodes and nnz entries
+ * needs under options opt (NULL = defaults; the degree thresholds matter)
  * (ipgc_color_ex grows the context's workspace to this size when needed).
  */
-IPGC_API size_t ipgc_workspace_size(int32_t n);
+IPGC_API size_t ipgc_workspace_size(int32_t n, int64_t nnz, const ipgc_options* opt);
 
 /*
  * Colour one graph (Section II-C's loop with Section IV's hybrid schedule).

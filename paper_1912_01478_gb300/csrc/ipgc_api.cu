@@ -12,7 +12,7 @@ using ipgc::Params;
 struct ipgc_ctx {
   int device = 0;
   int num_sms = 0;
-  int occ_persistent = 0;  // resident CTAs per SM of the persistent kernel
+  int occ256 = 0, occ512 = 0;  // resident CTAs per SM of the persistent kernel
   // workspace for one colouring: tent, worklists, static lists
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -64,14 +64,47 @@ int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
   } while (0)
 
-// Workspace: tent[n], worklists [2 parities][3 buckets][n], static lists
-// [mid][n] and [big][n], each 256-byte aligned.
-constexpr int kWsArrays = 1 + 2 * ipgc::NB + 2;
+// Workspace of one colouring, every array 256-byte aligned:
+//   tent[n]; low-degree worklists [2 parities][n]; work items (int4) of the
+//   high-degree nodes [2 parities + static][item_cap]; merge state of nodes
+//   with several items: bits [gcap][kGWords], done_a, done_d, flag [gcap].
+// A node of degree > t1 has more than t1 entries, so at most nnz / (t1 + 1)
+// exist, with at most nnz / chunk + (their number) items; a node with several
+// items has more than `chunk` entries.
+struct WsLayout {
+  size_t a4n, items_bytes, gbits_bytes, gint_bytes, total;
+};
 
-size_t ws_bytes_for(int32_t n) { return (size_t)kWsArrays * align256((size_t)n * sizeof(int32_t)); }
+int effective_t1(const ipgc_options& o) {
+  return o.t1 > 0 ? (o.t1 < ipgc::kMaxT1 ? o.t1 : ipgc::kMaxT1) : ipgc::kDefaultT1;
+}
 
-int ensure_ws(ipgc_ctx* ctx, int32_t n) {
-  const size_t need = ws_bytes_for(n);
+int effective_chunk(const ipgc_options& o) {
+  if (o.chunk <= 0) return ipgc::kDefaultChunk;
+  if (o.chunk < ipgc::kMinChunk) return ipgc::kMinChunk;
+  return o.chunk > ipgc::kMaxChunk ? ipgc::kMaxChunk : o.chunk;
+}
+
+WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk) {
+  WsLayout L;
+  L.a4n = align256((size_t)n * sizeof(int32_t));
+  int64_t nbig = nnz / ((int64_t)t1 + 1);
+  if (nbig > n) nbig = n;
+  const int64_t item_cap = nnz / chunk + nbig + 1;
+  const int64_t gcap = nnz / ((int64_t)chunk + 1) + 1;
+  L.items_bytes = align256((size_t)item_cap * sizeof(int4));
+  L.gbits_bytes = align256((size_t)gcap * ipgc::kGWords * sizeof(uint32_t));
+  L.gint_bytes = align256((size_t)gcap * sizeof(int32_t));
+  L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes;
+  return L;
+}
+
+size_t ws_bytes_for(int32_t n, int64_t nnz, const ipgc_options& o) {
+  return ws_layout(n, nnz, effective_t1(o), effective_chunk(o)).total;
+}
+
+int ensure_ws(ipgc_ctx* ctx, int32_t n, int64_t nnz, const ipgc_options& o) {
+  const size_t need = ws_bytes_for(n, nnz, o);
   if (ctx->ws_bytes >= need && ctx->ws) return IPGC_OK;
   if (ctx->ws) {
     cudaFree(ctx->ws);
@@ -102,26 +135,34 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.n = n;
   p.nnz = nnz;
   p.color = colors;
-  const size_t a = align256((size_t)n * sizeof(int32_t));
+  p.t1 = effective_t1(o);
+  p.chunk = effective_chunk(o);
+  const WsLayout L = ws_layout(n, nnz, p.t1, p.chunk);
+  const size_t a = L.a4n;
   char* w = ctx->ws;
   p.tent = (int32_t*)w;
   w += a;
-  for (int par = 0; par < 2; ++par)
-    for (int b = 0; b < ipgc::NB; ++b) {
-      p.wl[par][b] = (int32_t*)w;
-      w += a;
-    }
-  p.stat[ipgc::B_SMALL] = nullptr;
-  p.stat[ipgc::B_MID] = (int32_t*)w;
+  p.wl[0] = (int32_t*)w;
   w += a;
-  p.stat[ipgc::B_BIG] = (int32_t*)w;
+  p.wl[1] = (int32_t*)w;
+  w += a;
+  p.items[0] = (int4*)w;
+  w += L.items_bytes;
+  p.items[1] = (int4*)w;
+  w += L.items_bytes;
+  p.istat = (int4*)w;
+  w += L.items_bytes;
+  p.gbits = (uint32_t*)w;
+  w += L.gbits_bytes;
+  p.done_a = (int32_t*)w;
+  w += L.gint_bytes;
+  p.done_d = (int32_t*)w;
+  w += L.gint_bytes;
+  p.flag = (int32_t*)w;
   p.ctrl = ctx->d_ctrl;
   p.trace = o.trace;
   p.fin = o.fin_round;
   p.trace_cap = o.trace ? o.trace_cap : 0;
-  p.t1 = o.t1 > 0 ? (o.t1 < ipgc::kMaxT1 ? o.t1 : ipgc::kMaxT1) : ipgc::kDefaultT1;
-  p.t2 = o.t2 > 0 ? (o.t2 < ipgc::kMaxT2 ? o.t2 : ipgc::kMaxT2) : ipgc::kDefaultT2;
-  if (p.t2 < p.t1) p.t2 = p.t1;
   double h = (double)o.threshold_frac * (double)n;
   if (h < 0) h = 0;
   p.H = (int64_t)h;  // floor for h >= 0
@@ -130,6 +171,7 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
   p.mlp = (o.mode == IPGC_MODE_LEARNED) ? ctx->d_mlp : nullptr;
   p.bar_extra = o.fault_inject ? 1u : 0u;
+  p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
 }
 
 void stats_from_ctrl(const Ctrl& c, ipgc_stats* st) {
@@ -162,15 +204,15 @@ int run_validate(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32
   return *ctx->h_err ? IPGC_ERR_INVALID : IPGC_OK;
 }
 
-int run_hostloop(ipgc_ctx* ctx, const Params& p, int blocks, cudaStream_t s) {
-  IPGC_CUDA(ctx, ipgc::launch_round1(p, blocks, s));
+int run_hostloop(ipgc_ctx* ctx, const Params& p, int bs, int blocks, cudaStream_t s) {
+  IPGC_CUDA(ctx, ipgc::launch_round1(p, bs, blocks, s));
   int r = 2;
   for (;; ++r) {
     IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctrl, ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     IPGC_CUDA(ctx, cudaStreamSynchronize(s));
     const int par = r & 1;
     const int64_t total =
-        (int64_t)ctx->h_ctrl->cnt[par][0] + ctx->h_ctrl->cnt[par][1] + ctx->h_ctrl->cnt[par][2];
+        (int64_t)ctx->h_ctrl->cnt[par][ipgc::B_SMALL] + ctx->h_ctrl->cnt[par][ipgc::B_BIG];
     if (total == 0) break;
     if (r > p.max_rounds) {
       ctx->h_ctrl->status = IPGC_ERR_NO_CONVERGE;
@@ -185,8 +227,8 @@ int run_hostloop(ipgc_ctx* ctx, const Params& p, int blocks, cudaStream_t s) {
       mode = IPGC_MODE_DATA;
     else
       mode = total > p.H ? IPGC_MODE_TOPO : IPGC_MODE_DATA;
-    IPGC_CUDA(ctx, ipgc::launch_assign(p, blocks, r, mode, s));
-    IPGC_CUDA(ctx, ipgc::launch_detect(p, blocks, r, mode, s));
+    IPGC_CUDA(ctx, ipgc::launch_assign(p, bs, blocks, r, mode, s));
+    IPGC_CUDA(ctx, ipgc::launch_detect(p, bs, blocks, r, mode, s));
   }
   IPGC_CUDA(ctx, ipgc::launch_finish(p, r - 1, s));
   return IPGC_OK;
@@ -223,7 +265,15 @@ const char* ipgc_strerror(int s) {
   }
 }
 
-size_t ipgc_workspace_size(int32_t n) { return n > 0 ? ws_bytes_for(n) + align256(sizeof(Ctrl)) : 0; }
+size_t ipgc_workspace_size(int32_t n, int64_t nnz, const ipgc_options* opt) {
+  if (n <= 0 || nnz < 0) return 0;
+  ipgc_options o;
+  if (opt)
+    o = *opt;
+  else
+    ipgc_options_default(&o);
+  return ws_bytes_for(n, nnz, o) + align256(sizeof(Ctrl));
+}
 
 int ipgc_ctx_create(ipgc_ctx** out, int device) {
   if (!out) return IPGC_ERR_INVALID;
@@ -239,13 +289,14 @@ int ipgc_ctx_create(ipgc_ctx** out, int device) {
   int coop = 0;
   cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
-  if (e == cudaSuccess) e = ipgc::occupancy_persistent(&ctx->occ_persistent);
+  if (e == cudaSuccess) e = ipgc::occupancy_persistent(256, &ctx->occ256);
+  if (e == cudaSuccess) e = ipgc::occupancy_persistent(512, &ctx->occ512);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_err, sizeof(int));
   if (e != cudaSuccess) rc = cuda_fail(ctx, e);
-  if (rc == IPGC_OK && (!coop || ctx->occ_persistent < 1)) rc = IPGC_ERR_UNSUPPORTED;
+  if (rc == IPGC_OK && (!coop || ctx->occ256 < 1 || ctx->occ512 < 1)) rc = IPGC_ERR_UNSUPPORTED;
   if (rc != IPGC_OK) {
     ipgc_ctx_destroy(ctx);
     return rc;
@@ -287,7 +338,7 @@ int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int3
     ipgc_options_default(&o);
   if (o.mode < IPGC_MODE_THRESHOLD || o.mode > IPGC_MODE_LEARNED) return IPGC_ERR_INVALID;
   if (o.driver != IPGC_DRIVER_PERSISTENT && o.driver != IPGC_DRIVER_HOSTLOOP) return IPGC_ERR_INVALID;
-  if (o.block_size != 0 && o.block_size != ipgc::kBlock) return IPGC_ERR_UNSUPPORTED;
+  if (o.block_size != 0 && o.block_size != 256 && o.block_size != 512) return IPGC_ERR_UNSUPPORTED;
   if (o.trace && o.trace_cap < 0) return IPGC_ERR_INVALID;
   if (!(o.threshold_frac >= 0.0f)) return IPGC_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
@@ -303,7 +354,7 @@ int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int3
     return IPGC_OK;
   }
   ctx->last_trivial = 0;
-  rc = ensure_ws(ctx, n);
+  rc = ensure_ws(ctx, n, nnz, o);
   if (rc != IPGC_OK) return rc;
   if (o.validate) {
     rc = run_validate(ctx, rowptr, col, n, nnz, s);
@@ -312,13 +363,14 @@ int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int3
   Params p;
   fill_params(ctx, p, rowptr, col, n, nnz, colors_out, o);
   IPGC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctrl, 0, sizeof(Ctrl), s));
-  int bps = ctx->occ_persistent;
+  const int bs = o.block_size ? o.block_size : ipgc::kBlock;
+  int bps = bs == 256 ? ctx->occ256 : ctx->occ512;
   if (o.blocks_per_sm > 0 && o.blocks_per_sm < bps) bps = o.blocks_per_sm;
   const int blocks = bps * ctx->num_sms;
   if (o.driver == IPGC_DRIVER_PERSISTENT) {
-    IPGC_CUDA(ctx, ipgc::launch_persistent(p, blocks, s));
+    IPGC_CUDA(ctx, ipgc::launch_persistent(p, bs, blocks, s));
   } else {
-    rc = run_hostloop(ctx, p, blocks, s);
+    rc = run_hostloop(ctx, p, bs, blocks, s);
     if (rc != IPGC_OK) return rc;
   }
   IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctrl, ctx->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));

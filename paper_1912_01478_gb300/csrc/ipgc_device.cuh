@@ -1,7 +1,6 @@
 // Device-side building blocks of the hybrid IPGC loop: control block, kernel
-// parameters, bounded grid barrier, warp-aggregated worklist push and the
-// degree buckets. Shared by the single-graph colouring kernel and the
-// host-loop driver.
+// parameters, bounded grid barrier, warp-aggregated worklist pushes and the
+// degree buckets. Shared by the single-graph kernels and the host-loop driver.
 #pragma once
 
 #include <cstdint>
@@ -14,20 +13,26 @@ constexpr unsigned FULL = 0xffffffffu;
 
 // Degree buckets (the paper's Nested Parallelism, Section V): a node of
 // degree <= t1 is handled by one lane of a warp that colours 32 such nodes
-// together, t1 < degree <= t2 by one warp, above t2 by one CTA.
-enum Bucket : int { B_SMALL = 0, B_MID = 1, B_BIG = 2, NB = 3 };
+// together; a node of higher degree is cut into work items of `chunk`
+// neighbours, one warp each, and the warp that finishes its last item
+// completes it.
+enum Bucket : int { B_SMALL = 0, B_BIG = 1, NB = 2 };
 
-constexpr int kMaxT1 = 63;     // 64-bit lane mask covers colours 1..64
-constexpr int kMaxT2 = 1023;   // per-warp bitmap covers colours 1..1024
+constexpr int kMaxT1 = 63;       // 64-bit lane mask covers colours 1..64
 constexpr int kDefaultT1 = 24;
-constexpr int kDefaultT2 = 1023;
-constexpr int kBigWords = 2048;  // CTA bitmap window: 65536 colours
+constexpr int kDefaultChunk = 1024;
+constexpr int kMinChunk = 32;
+constexpr int kMaxChunk = 4096;
+constexpr int kGWords = 64;      // per-warp / per-node bitmap: colours 1..2048
+constexpr int kStageSmall = 128; // per-warp staging of low-degree pushes
+constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
 
 // Per-colouring control block in device memory. Zeroed before every launch.
 struct Ctrl {
-  int32_t cnt[2][4];               // worklist size per parity and bucket
-  int32_t nstat[4];                // static lists of mid / big nodes (topology sweeps)
-  uint32_t grab[2][4];             // dynamic work counters per parity
+  int32_t cnt[2][4];               // worklist size per parity: [B_SMALL] nodes, [B_BIG] nodes
+  int32_t icnt[2];                 // work items of the worklist's high-degree nodes, per parity
+  int32_t nistat;                  // work items of every high-degree node (topology sweeps)
+  int32_t ngslot;                  // merge-state slots handed out (multi-item nodes)
   unsigned long long dsum[2];      // sum of degrees of the worklist being built
   int32_t maxc;                    // largest committed colour
   int32_t status;                  // IPGC_OK or an IPGC_ERR_* code
@@ -40,9 +45,6 @@ struct Ctrl {
   int32_t pad[8];
 };
 
-// grab[] slots
-enum { G_ASSIGN_BIG = 0, G_DETECT_BIG = 1 };
-
 struct Params {
   const int32_t* __restrict__ rowptr;
   const int32_t* __restrict__ col;
@@ -50,19 +52,28 @@ struct Params {
   int64_t nnz;
   int32_t* color;    // committed colours (the caller's output buffer)
   int32_t* tent;     // tentative colours
-  int32_t* wl[2][NB];
-  int32_t* stat[NB];  // [B_MID], [B_BIG]: every node of that bucket
+  int32_t* wl[2];    // worklist of low-degree nodes, per parity
+  // high-degree nodes are held as work items {v, chunk index, gslot, #chunks}
+  // where gslot indexes the merge state of a node with more than one chunk
+  // (-1 otherwise)
+  int4* items[2];     // the worklist's items, per parity
+  int4* istat;        // items of every high-degree node (topology sweeps)
+  uint32_t* gbits;    // [gslot][kGWords] colours seen by finished chunks (kept zero)
+  int32_t* done_a;    // [gslot] chunks finished in the assignment step (kept zero)
+  int32_t* done_d;    // [gslot] chunks finished in the conflict step (kept zero)
+  int32_t* flag;      // [gslot] a chunk found a conflict (kept zero)
   Ctrl* ctrl;
   ipgc_trace_rec* trace;
   int32_t* fin;       // optional: round in which each node's colour was committed
   int32_t trace_cap;
-  int32_t t1, t2;
+  int32_t t1, chunk;
   int64_t H;          // topology-driven iff |WL| > H
   int32_t policy;     // IPGC_MODE_*
   int32_t max_rounds;
   uint64_t timeout_ns;
   const float* mlp;   // learned policy weights (device) or nullptr
   uint32_t bar_extra; // tests only: phantom CTAs every grid barrier waits for
+  int32_t col_vec;    // col is 16-byte aligned: int4 loads and bulk L2 prefetches allowed
 };
 
 __device__ __forceinline__ uint64_t gtime() {
@@ -73,14 +84,27 @@ __device__ __forceinline__ uint64_t gtime() {
 
 // Loads of data written by other CTAs during this launch bypass L1.
 __device__ __forceinline__ int32_t ld_cg(const int32_t* p) { return __ldcg(p); }
+
+// The same for the colour arrays gathered at random (committed and tentative
+// colours, 4n bytes each): L1 bypassed, and the L2 line marked evict-last so
+// the streamed neighbour lists do not push the colours out of L2.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ int32_t ld_keep(const int32_t* p, uint64_t pol) {
+  int32_t v;
+  asm volatile("ld.global.cg.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int4 ld_cg4(const int4* p) { return __ldcg(p); }
 // Loads of the read-only graph.
 __device__ __forceinline__ int32_t ld_ro(const int32_t* p) { return __ldg(p); }
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
-__device__ __forceinline__ int bucket_of(int d, int t1, int t2) {
-  return d <= t1 ? B_SMALL : (d <= t2 ? B_MID : B_BIG);
-}
+__device__ __forceinline__ int bucket_of(int d, int t1) { return d <= t1 ? B_SMALL : B_BIG; }
 
 // Grid-wide barrier for a cooperative launch, bounded by timeout_ns: a CTA
 // that waits longer records IPGC_ERR_TIMEOUT and leaves the barrier. Returns
@@ -104,7 +128,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, uint3
           atomicCAS(&c->status, 0, IPGC_ERR_TIMEOUT);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -128,12 +152,85 @@ __device__ __forceinline__ void warp_push(bool pred, int32_t v, int32_t* list, i
   if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = v;
 }
 
+// The same, staged: lanes append to a per-warp buffer in shared memory and
+// the warp reserves space in the global list once per buffer-full (and at
+// the end of the phase), so one atomic serves up to `cap` pushes.
+struct WarpStage {
+  int32_t* buf;  // this warp's shared buffer
+  int fill;      // entries in buf (warp-uniform)
+};
+
+__device__ __forceinline__ void stage_flush(WarpStage& st, int32_t* list, int32_t* counter) {
+  if (st.fill == 0) return;
+  __syncwarp();
+  const int lane = lane_id();
+  int base = 0;
+  if (lane == 0) base = atomicAdd(counter, st.fill);
+  base = __shfl_sync(FULL, base, 0);
+  for (int i = lane; i < st.fill; i += 32) list[base + i] = st.buf[i];
+  __syncwarp();
+  st.fill = 0;
+}
+
+__device__ __forceinline__ void stage_push(WarpStage& st, int cap, bool pred, int32_t v,
+                                           int32_t* list, int32_t* counter) {
+  const unsigned m = __ballot_sync(FULL, pred);
+  if (m == 0) return;
+  const int lane = lane_id();
+  if (pred) st.buf[st.fill + __popc(m & ((1u << lane) - 1u))] = v;
+  st.fill += __popc(m);
+  if (st.fill > cap - 32) stage_flush(st, list, counter);
+}
+
+// Staged append of work items: every lane may add the `cnt` items
+// {v, j, gslot, cnt}, j < cnt, of one node (cnt = 0: none); one atomic per
+// stage-full. All 32 lanes must call it.
+struct ItemStage {
+  int4* buf;  // this warp's shared buffer of kStageItems entries
+  int fill;   // entries in buf (warp-uniform)
+};
+
+__device__ __forceinline__ void items_flush(ItemStage& st, int4* list, int32_t* counter) {
+  if (st.fill == 0) return;
+  __syncwarp();
+  const int lane = lane_id();
+  int base = 0;
+  if (lane == 0) base = atomicAdd(counter, st.fill);
+  base = __shfl_sync(FULL, base, 0);
+  for (int i = lane; i < st.fill; i += 32) list[base + i] = st.buf[i];
+  __syncwarp();
+  st.fill = 0;
+}
+
+__device__ __forceinline__ void items_push(ItemStage& st, int v, int cnt, int gslot, int4* list,
+                                           int32_t* counter) {
+  const int lane = lane_id();
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int tot = __shfl_sync(FULL, incl, 31);
+  if (tot == 0) return;
+  const int excl = incl - cnt;
+  if (tot > kStageItems) {  // more than a stage: reserve room directly
+    int base = 0;
+    if (lane == 0) base = atomicAdd(counter, tot);
+    base = __shfl_sync(FULL, base, 0);
+    for (int j = 0; j < cnt; ++j) list[base + excl + j] = make_int4(v, j, gslot, cnt);
+    return;
+  }
+  if (st.fill + tot > kStageItems) items_flush(st, list, counter);
+  for (int j = 0; j < cnt; ++j) st.buf[st.fill + excl + j] = make_int4(v, j, gslot, cnt);
+  __syncwarp();
+  st.fill += tot;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
   return x;
 }
-
-__device__ __forceinline__ int warp_max(int x) { return __reduce_max_sync(FULL, x); }
 
 }  // namespace ipgc

@@ -88,7 +88,7 @@ class Options(ctypes.Structure):
         ("timeout_ns", ctypes.c_uint64),
         ("validate", ctypes.c_int32),
         ("t1", ctypes.c_int32),
-        ("t2", ctypes.c_int32),
+        ("chunk", ctypes.c_int32),
         ("block_size", ctypes.c_int32),
         ("blocks_per_sm", ctypes.c_int32),
         ("trace", ctypes.c_void_p),
@@ -115,7 +115,7 @@ SIGNATURES = {
     "ipgc_ctx_create": (_INT, [ctypes.POINTER(_P), _INT]),
     "ipgc_ctx_destroy": (_INT, [_P]),
     "ipgc_ctx_cuda_error": (_INT, [_P]),
-    "ipgc_workspace_size": (ctypes.c_size_t, [_I32]),
+    "ipgc_workspace_size": (ctypes.c_size_t, [_I32, _I64, ctypes.POINTER(Options)]),
     "ipgc_color": (_INT, [_P, _P, _I32, _I64, _P, ctypes.POINTER(Stats)]),
     "ipgc_color_ex": (
         _INT,
@@ -156,7 +156,7 @@ class ColorOptions:
     timeout_ns: int = 0
     validate: bool = True
     t1: int = 0
-    t2: int = 0
+    chunk: int = 0
     block_size: int = 0
     blocks_per_sm: int = 0
     fault_inject: int = 0
@@ -170,7 +170,7 @@ class ColorOptions:
         o.max_rounds = self.max_rounds
         o.timeout_ns = self.timeout_ns
         o.validate = 1 if self.validate else 0
-        o.t1, o.t2 = self.t1, self.t2
+        o.t1, o.chunk = self.t1, self.chunk
         o.block_size, o.blocks_per_sm = self.block_size, self.blocks_per_sm
         o.trace = trace_ptr or None
         o.trace_cap = trace_cap

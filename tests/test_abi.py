@@ -77,8 +77,13 @@ def test_strerror_and_defaults(lib):
 
 
 def test_workspace_size(lib):
-    assert lib.ipgc_workspace_size(0) == 0
-    assert lib.ipgc_workspace_size(1000) >= 9 * 4000
+    assert lib.ipgc_workspace_size(0, 0, None) == 0
+    assert lib.ipgc_workspace_size(1000, 8000, None) >= 3 * 4000  # tent + 2 worklists
+    # smaller t2: more high-degree nodes possible, more work-item room
+    o = ipgc.Options()
+    lib.ipgc_options_default(ctypes.byref(o))
+    o.t1 = 2
+    assert lib.ipgc_workspace_size(1000, 8000, ctypes.byref(o)) > lib.ipgc_workspace_size(1000, 8000, None)
 
 
 def test_host_validation(lib):

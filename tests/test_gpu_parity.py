@@ -146,13 +146,14 @@ def test_paths(ctx, n):
     assert np.array_equal(got, np.array([1 + i % 2 for i in range(n)])) and st.rounds == n // 2 + 1
 
 
-@pytest.mark.parametrize("t1,t2", [(0, 0), (1, 4), (3, 16), (8, 8), (63, 64), (63, 1023), (1, 1)])
-def test_bucket_thresholds(ctx, t1, t2):
-    # the same graph through every split of nodes between the three buckets
+@pytest.mark.parametrize("t1,chunk", [(0, 0), (1, 32), (3, 64), (8, 100), (63, 4096), (24, 33), (1, 4096)])
+def test_bucket_thresholds(ctx, t1, chunk):
+    # the same graph through every split of nodes between the low-degree path
+    # and chunked work items, with ragged chunk sizes
     rp, cl = graphgen.rmat(13, 16, seed=11)
     ref = oracle.color(rp, cl)
     for mode in ("threshold", "topo", "data"):
-        assert_parity(ctx, rp, cl, ref, mode=mode, t1=t1, t2=t2)
+        assert_parity(ctx, rp, cl, ref, mode=mode, t1=t1, chunk=chunk)
 
 
 @pytest.mark.parametrize("frac", [0.0, 0.3, 0.6, 0.9, 1.0, 5.0])
