@@ -63,6 +63,7 @@ extern "C" {
 #define IPGC_ERR_BUSY (-6)        /* server: request not admissible right now */
 #define IPGC_ERR_UNSUPPORTED (-7) /* option combination not available */
 #define IPGC_ERR_NOT_FOUND (-8)   /* server: unknown ticket */
+#define IPGC_ERR_TOO_LARGE (-9)   /* graph above a fixed-size entry point's limits */
 
 /* Mode policy: how each round chooses topology- or data-driven work. */
 #define IPGC_MODE_THRESHOLD 0 /* topology iff |WL| > floor(threshold_frac * n) (Section IV) */
@@ -193,6 +194,32 @@ IPGC_API int ipgc_color_host(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t
  */
 IPGC_API int ipgc_validate_csr(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
                       int64_t nnz, int on_device, void* stream);
+
+/*
+ * Colour one graph without allocating anything (the paper has no counterpart;
+ * this exists for callers that cannot allocate device memory when they need
+ * a colouring, e.g. code running inside an allocator or memory-pool callback,
+ * or under a budget reserved up front). Same result as ipgc_color_ex with
+ * default options; the CSR is always validated.
+ *   rowptr, col   device pointers as for ipgc_color_ex
+ *   n, nnz        at most IPGC_NOALLOC_MAX_N nodes and IPGC_NOALLOC_MAX_NNZ
+ *                 entries; larger graphs return IPGC_ERR_TOO_LARGE before any
+ *                 CUDA call
+ *   colors_out    device pointer, int32[n]
+ *   stats_out     host pointer or NULL; non-NULL waits for the stream
+ *   stream        cudaStream_t or NULL
+ * Working memory is one fixed device array inside the library (about 25 MB,
+ * held on every GPU that loads the library until the process exits), shared
+ * by all calls: calls that overlap on one GPU race and must be serialised by
+ * the caller. No cudaMalloc or cudaFree is made. The first call on a device
+ * looks up the array's device address, so make it before any stream capture.
+ * Errors: IPGC_ERR_INVALID, IPGC_ERR_TOO_LARGE, IPGC_ERR_TIMEOUT,
+ * IPGC_ERR_NO_CONVERGE, IPGC_ERR_CUDA, IPGC_ERR_UNSUPPORTED.
+ */
+#define IPGC_NOALLOC_MAX_N 524288
+#define IPGC_NOALLOC_MAX_NNZ 8388608
+IPGC_API int ipgc_color_noalloc(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+                                int32_t* colors_out, ipgc_stats* stats_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -261,6 +261,7 @@ const char* ipgc_strerror(int s) {
     case IPGC_ERR_BUSY: return "not admissible now (busy)";
     case IPGC_ERR_UNSUPPORTED: return "unsupported option";
     case IPGC_ERR_NOT_FOUND: return "unknown ticket";
+    case IPGC_ERR_TOO_LARGE: return "graph exceeds the fixed scratch of this entry point";
     default: return "unknown status";
   }
 }

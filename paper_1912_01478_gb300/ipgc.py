@@ -26,6 +26,11 @@ IPGC_ERR_CUDA = -5
 IPGC_ERR_BUSY = -6
 IPGC_ERR_UNSUPPORTED = -7
 IPGC_ERR_NOT_FOUND = -8
+IPGC_ERR_TOO_LARGE = -9
+
+# limits of ipgc_color_noalloc's fixed scratch
+NOALLOC_MAX_N = 524288
+NOALLOC_MAX_NNZ = 8388608
 
 MODE_THRESHOLD, MODE_TOPO, MODE_DATA, MODE_LEARNED = 0, 1, 2, 3
 DRIVER_PERSISTENT, DRIVER_HOSTLOOP = 0, 1
@@ -127,6 +132,7 @@ SIGNATURES = {
         [_P, _P, _P, _I32, _I64, _P, ctypes.POINTER(Stats), ctypes.POINTER(Options), _P],
     ),
     "ipgc_validate_csr": (_INT, [_P, _P, _P, _I32, _I64, _INT, _P]),
+    "ipgc_color_noalloc": (_INT, [_P, _P, _I32, _I64, _P, ctypes.POINTER(Stats), _P]),
 }
 
 
@@ -320,3 +326,26 @@ def color(rowptr, col, colors_out=None, options: ColorOptions | None = None, str
     """ipgc_color_ex on the default context of the tensors' device."""
     dev = rowptr.device.index or 0
     return default_context(dev).color(rowptr, col, colors_out, options, stream, trace)
+
+
+def color_noalloc(rowptr, col, colors_out=None, stream=None):
+    """ipgc_color_noalloc: colour without any allocation inside the library.
+
+    For callers that cannot allocate device memory at that moment; the library
+    works in one fixed device array (see include/ipgc.h for the limits), so
+    calls on one GPU must not overlap. colors_out must be given when the
+    caller itself cannot allocate (this helper only allocates it when absent).
+    """
+    import torch
+
+    n = rowptr.numel() - 1
+    nnz = col.numel()
+    if colors_out is None:
+        colors_out = torch.empty(max(n, 0), dtype=torch.int32, device=rowptr.device)
+    st = Stats()
+    rc = lib().ipgc_color_noalloc(
+        rowptr.data_ptr(), col.data_ptr() if nnz else None, n, nnz,
+        colors_out.data_ptr() if n else None, ctypes.byref(st), _stream_handle(stream) or None,
+    )
+    _check(rc, "ipgc_color_noalloc")
+    return colors_out, st
