@@ -196,6 +196,47 @@ IPGC_API int ipgc_validate_csr(ipgc_ctx* ctx, const int32_t* rowptr, const int32
                       int64_t nnz, int on_device, void* stream);
 
 /*
+ * Batched colouring: many independent graphs in one persistent launch. Each
+ * graph gets exactly the colouring ipgc_color_ex would give it alone (own
+ * worklists, rounds and mode decisions, Sections II-C and IV); graphs with at
+ * least team_min_nnz entries are coloured by teams of team_size CTAs, the
+ * others by one CTA each. Options in `base` apply to every graph (trace,
+ * fin_round, driver, blocks_per_sm and fault_inject are ignored).
+ */
+typedef struct ipgc_batch_options {
+  ipgc_options base;     /* defaults as ipgc_options_default, but validate = 0 */
+  int32_t team_size;     /* CTAs per team for large graphs (1..64); default 8 */
+  int32_t reserved;
+  int64_t team_min_nnz;  /* entries from which a graph goes to a team; default 262144 */
+} ipgc_batch_options;
+
+IPGC_API void ipgc_batch_options_default(ipgc_batch_options* opt);
+
+/*
+ *   num_graphs   G >= 0
+ *   node_off     HOST pointer, int64[G + 1]: graph g has nodes
+ *                [node_off[g], node_off[g + 1]) of the concatenation
+ *   edge_off     HOST pointer, int64[G + 1]: graph g's entries in col_cat
+ *   rowptr_cat   device pointer: graph g's local rowptr (n_g + 1 entries,
+ *                values in [0, nnz_g]) starts at rowptr_cat[node_off[g] + g]
+ *   col_cat      device pointer: graph g's local neighbour IDs at edge_off[g]
+ *   colors_cat   device pointer, int32[node_off[G]]: graph g's colours at
+ *                node_off[g]
+ *   per_graph_stats  host pointer to G records, or NULL (then the call only
+ *                enqueues work on `stream`)
+ * The context keeps a batched workspace (about 12 bytes per node, 16 bytes
+ * per work item and 256 bytes per large node), grown on demand.
+ * Returns IPGC_OK or the first per-graph error (IPGC_ERR_INVALID for a bad
+ * graph when base.validate is set, IPGC_ERR_TIMEOUT, IPGC_ERR_NO_CONVERGE),
+ * IPGC_ERR_OOM, IPGC_ERR_CUDA.
+ */
+IPGC_API int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_off,
+                                const int64_t* edge_off, const int32_t* rowptr_cat,
+                                const int32_t* col_cat, int32_t* colors_cat,
+                                ipgc_stats* per_graph_stats, const ipgc_batch_options* opt,
+                                void* stream);
+
+/*
  * Colour one graph without allocating anything (the paper has no counterpart;
  * this exists for callers that cannot allocate device memory when they need
  * a colouring, e.g. code running inside an allocator or memory-pool callback,

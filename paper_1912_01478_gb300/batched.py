@@ -1,0 +1,92 @@
+"""Binding of the batched entry point (ctypes; argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import ipgc
+
+
+class BatchOptions(ctypes.Structure):
+    _fields_ = [
+        ("base", ipgc.Options),
+        ("team_size", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("team_min_nnz", ctypes.c_int64),
+    ]
+
+
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "ipgc_batch_options_default": (None, [ctypes.POINTER(BatchOptions)]),
+    "ipgc_color_batched": (
+        ctypes.c_int,
+        [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.POINTER(ipgc.Stats),
+         ctypes.POINTER(BatchOptions), _P],
+    ),
+}
+
+_bound = False
+
+
+def lib():
+    global _bound
+    L = ipgc.lib()
+    if not _bound:
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _bound = True
+    return L
+
+
+def options(team_size: int = 0, team_min_nnz: int = -1, **base) -> BatchOptions:
+    """Batch options: defaults, then team settings and ipgc.ColorOptions fields."""
+    o = BatchOptions()
+    lib().ipgc_batch_options_default(ctypes.byref(o))
+    if base:
+        b = ipgc.ColorOptions(**{"validate": False, **base}).to_c()
+        o.base = b
+    if team_size:
+        o.team_size = team_size
+    if team_min_nnz >= 0:
+        o.team_min_nnz = team_min_nnz
+    return o
+
+
+def color_batched(ctx: "ipgc.Context", node_off: np.ndarray, edge_off: np.ndarray, rowptr_cat,
+                  col_cat, colors_cat=None, opts: BatchOptions | None = None, stream=None,
+                  want_stats: bool = True):
+    """Colour every graph of a concatenated batch held in CUDA int32 tensors.
+
+    node_off / edge_off: host int64 arrays of G + 1 offsets. Returns
+    (colors_cat, stats) where stats is a numpy structured array (or None).
+    """
+    import torch
+
+    node_off = np.ascontiguousarray(node_off, dtype=np.int64)
+    edge_off = np.ascontiguousarray(edge_off, dtype=np.int64)
+    G = node_off.size - 1
+    total_n = int(node_off[-1])
+    if colors_cat is None:
+        colors_cat = torch.empty(max(total_n, 0), dtype=torch.int32, device=rowptr_cat.device)
+    st = (ipgc.Stats * max(G, 1))() if want_stats else None
+    rc = lib().ipgc_color_batched(
+        ctx.handle, G, node_off.ctypes.data, edge_off.ctypes.data, rowptr_cat.data_ptr(),
+        col_cat.data_ptr() if col_cat.numel() else None,
+        colors_cat.data_ptr() if total_n else None,
+        st if want_stats else None, ctypes.byref(opts) if opts is not None else None,
+        ipgc._stream_handle(stream) or None,
+    )
+    if rc != ipgc.IPGC_OK:
+        raise ipgc.IpgcError(rc, "ipgc_color_batched")
+    if not want_stats:
+        return colors_cat, None
+    arr = np.array([(s.rounds, s.num_colors, s.rounds_topo, s.rounds_data, s.edges_processed, s.ns,
+                     s.error) for s in st[:G]],
+                   dtype=[("rounds", np.int32), ("num_colors", np.int32), ("rounds_topo", np.int32),
+                          ("rounds_data", np.int32), ("edges_processed", np.int64),
+                          ("ns", np.uint64), ("error", np.int32)])
+    return colors_cat, arr

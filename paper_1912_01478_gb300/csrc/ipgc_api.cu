@@ -36,6 +36,25 @@ struct ipgc_ctx {
   int last_trivial = 0;  // n == 0
 };
 
+namespace ipgc {
+
+int effective_t1(const ipgc_options& o) {
+  return o.t1 > 0 ? (o.t1 < kMaxT1 ? o.t1 : kMaxT1) : kDefaultT1;
+}
+
+int effective_chunk(const ipgc_options& o) {
+  if (o.chunk <= 0) return kDefaultChunk;
+  if (o.chunk < kMinChunk) return kMinChunk;
+  return o.chunk > kMaxChunk ? kMaxChunk : o.chunk;
+}
+
+int ctx_device(const ipgc_ctx* ctx) { return ctx->device; }
+int ctx_num_sms(const ipgc_ctx* ctx) { return ctx->num_sms; }
+void ctx_note_cuda_error(ipgc_ctx* ctx, int err) { ctx->last_cuda = err; }
+const float* ctx_policy_weights(const ipgc_ctx* ctx) { return ctx->d_mlp; }
+
+}  // namespace ipgc
+
 namespace {
 
 struct DeviceGuard {
@@ -75,15 +94,8 @@ struct WsLayout {
   size_t a4n, items_bytes, gbits_bytes, gint_bytes, total;
 };
 
-int effective_t1(const ipgc_options& o) {
-  return o.t1 > 0 ? (o.t1 < ipgc::kMaxT1 ? o.t1 : ipgc::kMaxT1) : ipgc::kDefaultT1;
-}
-
-int effective_chunk(const ipgc_options& o) {
-  if (o.chunk <= 0) return ipgc::kDefaultChunk;
-  if (o.chunk < ipgc::kMinChunk) return ipgc::kMinChunk;
-  return o.chunk > ipgc::kMaxChunk ? ipgc::kMaxChunk : o.chunk;
-}
+using ipgc::effective_chunk;
+using ipgc::effective_t1;
 
 WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk) {
   WsLayout L;
@@ -319,6 +331,7 @@ int ipgc_ctx_destroy(ipgc_ctx* ctx) {
     if (ctx->d_col) cudaFree(ctx->d_col);
     if (ctx->d_colors) cudaFree(ctx->d_colors);
     if (ctx->d_mlp) cudaFree(ctx->d_mlp);
+    ipgc::batched_release(ctx);
   }
   delete ctx;
   return IPGC_OK;

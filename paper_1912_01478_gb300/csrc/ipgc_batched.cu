@@ -1,0 +1,391 @@
+// Batched hybrid IPGC: thousands of independent graphs in one persistent
+// cooperative launch.
+//
+// Every graph runs its own round loop (its own worklists, round counter, mode
+// decision and control block) with exactly the single-graph phases of
+// ipgc_phases.cuh, so each graph's colours equal those of colouring it alone.
+// Large graphs are coloured by teams of `team_size` CTAs that separate their
+// rounds with a bounded team barrier; the host deals them to the teams
+// largest-first onto the least-loaded team. Every other graph is coloured by
+// a single CTA that takes graphs, largest first, from a shared counter once
+// its team's list is done, so the short graphs fill the tail.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <queue>
+#include <vector>
+
+#include "ipgc_internal.h"
+#include "ipgc_phases.cuh"
+
+namespace ipgc {
+
+struct BatchParams {
+  const Params* params;       // [G] per-graph parameters
+  const int32_t* team_list;   // graphs of team t: team_list[team_off[t] .. team_off[t + 1])
+  const int32_t* team_off;    // [nteams + 1]
+  const int32_t* solo_list;   // graphs coloured by one CTA each, largest first
+  int32_t nsolo;
+  int32_t team_size;
+  int32_t nteams;
+  int32_t* solo_next;         // shared counter over solo_list (zeroed before launch)
+};
+
+template <int BS>
+__global__ void __launch_bounds__(BS, min_blocks(BS)) batched_kernel(BatchParams bp) {
+  __shared__ Smem<BS> sm;
+  __shared__ int s_k;
+  smem_clear<BS>(sm);
+  const int team = blockIdx.x / bp.team_size, rank = blockIdx.x % bp.team_size;
+  if (team < bp.nteams) {
+    for (int i = bp.team_off[team]; i < bp.team_off[team + 1]; ++i)
+      color_graph<BS>(bp.params[bp.team_list[i]], sm, Team{rank, bp.team_size});
+  }
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_k = atomicAdd(bp.solo_next, 1);
+    __syncthreads();
+    const int k = s_k;
+    if (k >= bp.nsolo) break;
+    color_graph<BS>(bp.params[bp.solo_list[k]], sm, Team{0, 1});
+  }
+}
+
+cudaError_t occupancy_batched(int bs, int* blocks_per_sm) {
+  return with_block(bs, [&](auto B) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, batched_kernel<decltype(B)::value>, decltype(B)::value, 0);
+  });
+}
+
+cudaError_t launch_batched(const BatchParams& bp, int bs, int blocks, cudaStream_t s) {
+  return with_block(bs, [&](auto B) {
+    BatchParams q = bp;
+    void* args[] = {&q};
+    return cudaLaunchCooperativeKernel((const void*)batched_kernel<decltype(B)::value>,
+                                       dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+  });
+}
+
+}  // namespace ipgc
+
+// ------------------------------------------------------------------ host --
+
+using ipgc::BatchParams;
+using ipgc::Ctrl;
+using ipgc::Params;
+
+namespace {
+
+inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct BatchWs {
+  int device = -1;
+  char* dev = nullptr;  // one device allocation, carved below
+  size_t dev_bytes = 0;
+  Ctrl* h_ctrl = nullptr;  // pinned copy of the per-graph control blocks
+  size_t h_ctrl_cap = 0;
+  int* h_err = nullptr;  // pinned
+  std::vector<Params> params;
+  std::vector<int32_t> lists;
+};
+
+// workspace kept per context (one batch at a time per context)
+struct BatchCtxSlot {
+  ipgc_ctx* ctx;
+  BatchWs ws;
+};
+std::vector<BatchCtxSlot*> g_slots;
+std::mutex g_slots_mu;
+
+BatchWs* ws_for(ipgc_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(g_slots_mu);
+  for (BatchCtxSlot* s : g_slots)
+    if (s->ctx == ctx) return &s->ws;
+  BatchCtxSlot* s = new (std::nothrow) BatchCtxSlot{ctx, BatchWs()};
+  if (!s) return nullptr;
+  g_slots.push_back(s);
+  return &s->ws;
+}
+
+int cuda_err(ipgc_ctx* ctx, cudaError_t e) {
+  ipgc::ctx_note_cuda_error(ctx, (int)e);
+  return e == cudaErrorMemoryAllocation ? IPGC_ERR_OOM : IPGC_ERR_CUDA;
+}
+
+#define BCUDA(call)                         \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_); \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+void ipgc_batch_options_default(ipgc_batch_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  ipgc_options_default(&o->base);
+  o->base.validate = 0;
+  o->team_size = 8;
+  o->team_min_nnz = 262144;
+}
+
+int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_off,
+                       const int64_t* edge_off, const int32_t* rowptr_cat, const int32_t* col_cat,
+                       int32_t* colors_cat, ipgc_stats* per_graph_stats,
+                       const ipgc_batch_options* opt, void* stream) {
+  if (!ctx || num_graphs < 0 || (num_graphs > 0 && (!node_off || !edge_off))) return IPGC_ERR_INVALID;
+  ipgc_batch_options o;
+  if (opt)
+    o = *opt;
+  else
+    ipgc_batch_options_default(&o);
+  if (o.team_size < 1 || o.team_size > 64) return IPGC_ERR_INVALID;
+  if (o.base.mode < IPGC_MODE_THRESHOLD || o.base.mode > IPGC_MODE_LEARNED) return IPGC_ERR_INVALID;
+  if (o.base.block_size != 0 && o.base.block_size != 256 && o.base.block_size != 512)
+    return IPGC_ERR_UNSUPPORTED;
+  if (num_graphs == 0) return IPGC_OK;
+  // graph shapes (host offsets)
+  if (node_off[0] != 0 || edge_off[0] != 0) return IPGC_ERR_INVALID;
+  const int64_t total_n = node_off[num_graphs], total_e = edge_off[num_graphs];
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
+    if (n < 0 || e < 0 || n >= INT32_MAX || e > INT32_MAX) return IPGC_ERR_INVALID;
+    if (e > 0 && n == 0) return IPGC_ERR_INVALID;
+  }
+  if (total_n > 0 && (!rowptr_cat || !colors_cat)) return IPGC_ERR_INVALID;
+  if (total_e > 0 && !col_cat) return IPGC_ERR_INVALID;
+
+  const int dev = ipgc::ctx_device(ctx);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != dev) cudaSetDevice(dev);
+  struct Restore {
+    int prev, dev;
+    ~Restore() {
+      if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+  } restore{prev, dev};
+  cudaStream_t s = (cudaStream_t)stream;
+
+  BatchWs* W = ws_for(ctx);
+  if (!W) return IPGC_ERR_OOM;
+  const int t1 = ipgc::effective_t1(o.base), chunk = ipgc::effective_chunk(o.base);
+  const int bs = o.base.block_size ? o.base.block_size : ipgc::kBlock;
+
+  // per-graph slices of the workspace
+  std::vector<int64_t> item_base(num_graphs + 1), gbase(num_graphs + 1);
+  item_base[0] = gbase[0] = 0;
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
+    int64_t nbig = e / (t1 + 1);
+    if (nbig > n) nbig = n;
+    item_base[g + 1] = item_base[g] + e / chunk + nbig + 1;
+    gbase[g + 1] = gbase[g] + e / ((int64_t)chunk + 1) + 1;
+  }
+  const size_t b_params = al256(sizeof(Params) * (size_t)num_graphs);
+  const size_t b_lists = al256(sizeof(int32_t) * ((size_t)2 * num_graphs + 64 * 1024 + 16));
+  const size_t b_ctrl = al256(sizeof(Ctrl) * (size_t)num_graphs);
+  const size_t b_node = al256(sizeof(int32_t) * (size_t)total_n);
+  const size_t b_items = al256(sizeof(int4) * (size_t)item_base[num_graphs]);
+  const size_t b_gbits = al256(sizeof(uint32_t) * ipgc::kGWords * (size_t)gbase[num_graphs]);
+  const size_t b_gint = al256(sizeof(int32_t) * (size_t)gbase[num_graphs]);
+  const size_t need = b_params + b_lists + b_ctrl + 3 * b_node + 3 * b_items + b_gbits + 3 * b_gint + 256;
+  if (W->dev_bytes < need || W->device != dev) {
+    if (W->dev) cudaFree(W->dev);
+    W->dev = nullptr;
+    W->dev_bytes = 0;
+    BCUDA(cudaMalloc((void**)&W->dev, need));
+    W->dev_bytes = need;
+    W->device = dev;
+  }
+  if (W->h_ctrl_cap < (size_t)num_graphs) {
+    if (W->h_ctrl) cudaFreeHost(W->h_ctrl);
+    W->h_ctrl = nullptr;
+    W->h_ctrl_cap = 0;
+    BCUDA(cudaMallocHost((void**)&W->h_ctrl, sizeof(Ctrl) * (size_t)num_graphs));
+    W->h_ctrl_cap = num_graphs;
+  }
+  if (!W->h_err) BCUDA(cudaMallocHost((void**)&W->h_err, sizeof(int)));
+  char* w = W->dev;
+  Params* d_params = (Params*)w;
+  w += b_params;
+  int32_t* d_lists = (int32_t*)w;
+  w += b_lists;
+  Ctrl* d_ctrl = (Ctrl*)w;
+  w += b_ctrl;
+  int32_t* d_tent = (int32_t*)w;
+  w += b_node;
+  int32_t* d_wl0 = (int32_t*)w;
+  w += b_node;
+  int32_t* d_wl1 = (int32_t*)w;
+  w += b_node;
+  int4* d_it0 = (int4*)w;
+  w += b_items;
+  int4* d_it1 = (int4*)w;
+  w += b_items;
+  int4* d_its = (int4*)w;
+  w += b_items;
+  uint32_t* d_gbits = (uint32_t*)w;
+  w += b_gbits;
+  int32_t* d_done_a = (int32_t*)w;
+  w += b_gint;
+  int32_t* d_done_d = (int32_t*)w;
+  w += b_gint;
+  int32_t* d_flag = (int32_t*)w;
+  w += b_gint;
+  int* d_err = (int*)w;
+
+  // optional validation of every graph (one launch per graph)
+  if (o.base.validate) {
+    BCUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    for (int32_t g = 0; g < num_graphs; ++g) {
+      const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
+      if (n == 0) continue;
+      int blocks = (int)std::min<int64_t>(1024, (n * 32 + 255) / 256);
+      BCUDA(ipgc::launch_validate(rowptr_cat + node_off[g] + g, col_cat + edge_off[g], (int32_t)n, e,
+                                  d_err, blocks, s));
+    }
+    BCUDA(cudaMemcpyAsync(W->h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BCUDA(cudaStreamSynchronize(s));
+    if (*W->h_err) return IPGC_ERR_INVALID;
+  }
+
+  // per-graph parameters
+  W->params.resize(num_graphs);
+  const float* d_mlp = ipgc::ctx_policy_weights(ctx);
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    Params& p = W->params[g];
+    std::memset(&p, 0, sizeof(p));
+    const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
+    p.rowptr = rowptr_cat + node_off[g] + g;
+    p.col = col_cat + edge_off[g];
+    p.n = (int32_t)n;
+    p.nnz = e;
+    p.color = colors_cat + node_off[g];
+    p.tent = d_tent + node_off[g];
+    p.wl[0] = d_wl0 + node_off[g];
+    p.wl[1] = d_wl1 + node_off[g];
+    p.items[0] = d_it0 + item_base[g];
+    p.items[1] = d_it1 + item_base[g];
+    p.istat = d_its + item_base[g];
+    p.gbits = d_gbits + (size_t)gbase[g] * ipgc::kGWords;
+    p.done_a = d_done_a + gbase[g];
+    p.done_d = d_done_d + gbase[g];
+    p.flag = d_flag + gbase[g];
+    p.ctrl = d_ctrl + g;
+    p.t1 = t1;
+    p.chunk = chunk;
+    double h = (double)o.base.threshold_frac * (double)n;
+    p.H = (int64_t)(h > 0 ? h : 0);
+    p.policy = o.base.mode;
+    p.max_rounds = o.base.max_rounds > 0 ? o.base.max_rounds : (int32_t)n + 1;
+    p.timeout_ns = o.base.timeout_ns ? o.base.timeout_ns : 10000000000ull;
+    p.mlp = o.base.mode == IPGC_MODE_LEARNED ? d_mlp : nullptr;
+    p.col_vec = ((uintptr_t)p.col & 15u) == 0 ? 1 : 0;
+  }
+
+  // schedule: large graphs to teams (largest first onto the least-loaded
+  // team), the rest to single CTAs in a shared queue, largest first
+  int occ = 0;
+  BCUDA(ipgc::occupancy_batched(bs, &occ));
+  const int sms = ipgc::ctx_num_sms(ctx);
+  int team_size = o.team_size;
+  int nteams = occ * sms / team_size;
+  if (nteams < 1) {
+    nteams = 1;
+    team_size = occ * sms;
+  }
+  const int blocks = std::max(nteams * team_size, occ * sms);
+  std::vector<int32_t> order(num_graphs);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return edge_off[a + 1] - edge_off[a] > edge_off[b + 1] - edge_off[b];
+  });
+  std::vector<std::vector<int32_t>> per_team(nteams);
+  std::vector<int32_t> solo;
+  using Load = std::pair<int64_t, int32_t>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int32_t t = 0; t < nteams; ++t) heap.push({0, t});
+  for (int32_t g : order) {
+    const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
+    if (n == 0) continue;
+    if (e >= o.team_min_nnz && team_size > 1) {
+      Load l = heap.top();
+      heap.pop();
+      per_team[l.second].push_back(g);
+      heap.push({l.first + e + n, l.second});
+    } else {
+      solo.push_back(g);
+    }
+  }
+  W->lists.clear();
+  std::vector<int32_t> team_off(nteams + 1, 0);
+  for (int32_t t = 0; t < nteams; ++t) {
+    team_off[t + 1] = team_off[t] + (int32_t)per_team[t].size();
+    W->lists.insert(W->lists.end(), per_team[t].begin(), per_team[t].end());
+  }
+  const size_t n_team_list = W->lists.size();
+  W->lists.insert(W->lists.end(), team_off.begin(), team_off.end());
+  W->lists.insert(W->lists.end(), solo.begin(), solo.end());
+  W->lists.push_back(0);  // solo queue counter
+  if (W->lists.size() * sizeof(int32_t) > b_lists) return IPGC_ERR_UNSUPPORTED;
+
+  BCUDA(cudaMemcpyAsync(d_params, W->params.data(), sizeof(Params) * (size_t)num_graphs,
+                        cudaMemcpyHostToDevice, s));
+  BCUDA(cudaMemcpyAsync(d_lists, W->lists.data(), sizeof(int32_t) * W->lists.size(),
+                        cudaMemcpyHostToDevice, s));
+  BCUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl) * (size_t)num_graphs, s));
+
+  BatchParams bp;
+  bp.params = d_params;
+  bp.team_list = d_lists;
+  bp.team_off = d_lists + n_team_list;
+  bp.solo_list = d_lists + n_team_list + (nteams + 1);
+  bp.nsolo = (int32_t)solo.size();
+  bp.team_size = team_size;
+  bp.nteams = nteams;
+  bp.solo_next = d_lists + n_team_list + (nteams + 1) + solo.size();
+  BCUDA(ipgc::launch_batched(bp, bs, blocks, s));
+
+  if (!per_graph_stats) return IPGC_OK;
+  BCUDA(cudaMemcpyAsync(W->h_ctrl, d_ctrl, sizeof(Ctrl) * (size_t)num_graphs,
+                        cudaMemcpyDeviceToHost, s));
+  BCUDA(cudaStreamSynchronize(s));
+  int worst = IPGC_OK;
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    const Ctrl& c = W->h_ctrl[g];
+    ipgc_stats& st = per_graph_stats[g];
+    std::memset(&st, 0, sizeof(st));
+    if (node_off[g + 1] == node_off[g]) continue;
+    st.rounds = c.rounds;
+    st.num_colors = c.maxc;
+    st.rounds_topo = c.rounds_topo;
+    st.rounds_data = c.rounds_data;
+    st.edges_processed = (int64_t)c.edges;
+    st.ns = c.t_end >= c.t_start ? c.t_end - c.t_start : 0;
+    st.error = c.status;
+    if (c.status != IPGC_OK && worst == IPGC_OK) worst = c.status;
+  }
+  return worst;
+}
+
+}  // extern "C"
+
+void ipgc::batched_release(ipgc_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(g_slots_mu);
+  for (size_t i = 0; i < g_slots.size(); ++i) {
+    if (g_slots[i]->ctx != ctx) continue;
+    BatchWs& W = g_slots[i]->ws;
+    if (W.dev) cudaFree(W.dev);
+    if (W.h_ctrl) cudaFreeHost(W.h_ctrl);
+    if (W.h_err) cudaFreeHost(W.h_err);
+    delete g_slots[i];
+    g_slots.erase(g_slots.begin() + i);
+    return;
+  }
+}

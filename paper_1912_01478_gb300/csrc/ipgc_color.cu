@@ -30,727 +30,9 @@
 #include <type_traits>
 
 #include "ipgc_internal.h"
+#include "ipgc_phases.cuh"
 
 namespace ipgc {
-
-enum { MODE_TOPO = IPGC_MODE_TOPO, MODE_DATA = IPGC_MODE_DATA };
-
-// Resident CTAs per SM each block size is compiled for: 512 threads x 2 caps
-// a thread at 64 registers, 256 x 3 at 85.
-constexpr int min_blocks(int bs) { return bs >= 512 ? 2 : 3; }
-
-template <int BS>
-struct Smem {
-  static constexpr int W = BS / 32;
-  unsigned small_w[W][64];          // per warp: two mask words per lane / loser flags
-  unsigned wbits[W][kGWords];       // per warp: bitmap of colours 1..2048 (work items)
-  int32_t stage_s[W][kStageSmall];  // staged pushes: low-degree losers
-  int4 stage_i[W][kStageItems];     // staged pushes: work items of high-degree losers
-  int4 stage_t[W][kStageItems];     // staged pushes: static work items (round 1)
-  unsigned long long red64[W];
-  int red[W];
-  unsigned red2[W];
-};
-
-template <int BS>
-__device__ __forceinline__ void smem_clear(Smem<BS>& sm) {
-  unsigned* w = &sm.small_w[0][0];
-  for (int i = threadIdx.x; i < Smem<BS>::W * 64; i += BS) w[i] = 0;
-  w = &sm.wbits[0][0];
-  for (int i = threadIdx.x; i < Smem<BS>::W * kGWords; i += BS) w[i] = 0;
-  __syncthreads();
-}
-
-template <int BS>
-__device__ __forceinline__ int block_max(Smem<BS>& sm, int x) {
-  const int warp = threadIdx.x >> 5, lane = lane_id();
-  x = __reduce_max_sync(FULL, x);
-  __syncthreads();
-  if (lane == 0) sm.red[warp] = x;
-  __syncthreads();
-  int y = lane < Smem<BS>::W ? sm.red[lane] : INT_MIN;
-  return __reduce_max_sync(FULL, y);
-}
-
-template <int BS>
-__device__ __forceinline__ unsigned long long block_sum64(Smem<BS>& sm, unsigned long long x) {
-  const int warp = threadIdx.x >> 5, lane = lane_id();
-  x = warp_sum_u64(x);
-  __syncthreads();
-  if (lane == 0) sm.red64[warp] = x;
-  __syncthreads();
-  unsigned long long y = lane < Smem<BS>::W ? sm.red64[lane] : 0ull;
-  return warp_sum_u64(y);
-}
-
-// Per-thread accumulators of one phase, merged once per CTA at its end.
-struct PhaseAcc {
-  int maxc = 0;                 // largest colour committed by this thread
-  unsigned long long dsum = 0;  // degrees of the nodes this thread pushed
-  unsigned long long nbig = 0;  // high-degree nodes this thread pushed
-};
-
-// One CTA-wide reduction of the three accumulators, then one atomic each.
-template <int BS>
-__device__ __forceinline__ void phase_commit(const Params& p, Smem<BS>& sm, const PhaseAcc& a,
-                                             int nxt) {
-  const int warp = threadIdx.x >> 5, lane = lane_id();
-  const int m = __reduce_max_sync(FULL, a.maxc);
-  const unsigned long long ds = warp_sum_u64(a.dsum);
-  const unsigned nb = __reduce_add_sync(FULL, (unsigned)a.nbig);
-  __syncthreads();  // previous users of the scratch slots are done
-  if (lane == 0) {
-    sm.red[warp] = m;
-    sm.red64[warp] = ds;
-    sm.red2[warp] = nb;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const bool in = lane < Smem<BS>::W;
-    const int mm = __reduce_max_sync(FULL, in ? sm.red[lane] : 0);
-    const unsigned long long dd = warp_sum_u64(in ? sm.red64[lane] : 0ull);
-    const unsigned bb = __reduce_add_sync(FULL, in ? sm.red2[lane] : 0u);
-    if (lane == 0) {
-      if (mm > 0) atomicMax(&p.ctrl->maxc, mm);
-      if (dd) atomicAdd(&p.ctrl->dsum[nxt], dd);
-      if (bb) atomicAdd(&p.ctrl->cnt[nxt][B_BIG], (int)bb);
-    }
-  }
-}
-
-__device__ __forceinline__ int num_chunks(int d, int chunk) { return (d + chunk - 1) / chunk; }
-
-// ---------------------------------------------------------------- round 1 --
-
-// Round 1: all nodes active, all tentative colours 1. v wins iff no
-// neighbour has a lower ID. Builds the worklist of round 2 (parity 0) and
-// the static work items of every high-degree node used by later topology
-// sweeps; hands out merge-state slots to nodes with several items.
-template <int BS>
-__device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc) {
-  Ctrl* c = p.ctrl;
-  const int warp = threadIdx.x >> 5, lane = lane_id();
-  WarpStage ss{sm.stage_s[warp], 0};
-  ItemStage si{sm.stage_i[warp], 0}, st{sm.stage_t[warp], 0};
-  for (int64_t base = (int64_t)blockIdx.x * BS; base < p.n; base += (int64_t)gridDim.x * BS) {
-    const int v = (int)(base + threadIdx.x);
-    const bool valid = v < p.n;
-    int d = 0;
-    bool lose = false;
-    if (valid) {
-      const int s = ld_ro(p.rowptr + v), e = ld_ro(p.rowptr + v + 1);
-      d = e - s;
-      lose = d > 0 && ld_ro(p.col + s) < v;
-      p.color[v] = lose ? 0 : 1;
-      p.tent[v] = lose ? 0 : 1;
-      if (!lose) acc.maxc = 1;
-      if (p.fin) p.fin[v] = lose ? 0 : 1;
-      if (lose) acc.dsum += (unsigned long long)d;
-    }
-    const bool big = valid && bucket_of(d, p.t1) == B_BIG;
-    stage_push(ss, kStageSmall, lose && !big, v, p.wl[0], &c->cnt[0][B_SMALL]);
-    const int nch = big ? num_chunks(d, p.chunk) : 0;
-    const bool multi = nch > 1;
-    const unsigned mm = __ballot_sync(FULL, multi);
-    int gslot = -1;
-    if (mm) {
-      int gb = 0;
-      if (lane == 0) gb = atomicAdd(&c->ngslot, __popc(mm));
-      gb = __shfl_sync(FULL, gb, 0);
-      if (multi) {
-        gslot = gb + __popc(mm & ((1u << lane) - 1u));
-        for (int i = 0; i < kGWords; ++i) p.gbits[(size_t)gslot * kGWords + i] = 0;
-        p.done_a[gslot] = 0;
-        p.done_d[gslot] = 0;
-        p.flag[gslot] = 0;
-      }
-    }
-    items_push(st, v, nch, gslot, p.istat, &c->nistat);
-    items_push(si, v, lose ? nch : 0, gslot, p.items[0], &c->icnt[0]);
-    if (big && lose) acc.nbig += 1;
-  }
-  stage_flush(ss, p.wl[0], &c->cnt[0][B_SMALL]);
-  items_flush(st, p.istat, &c->nistat);
-  items_flush(si, p.items[0], &c->icnt[0]);
-}
-
-// ------------------------------------------------------- small-degree nodes --
-//
-// A warp handles up to 32 nodes of degree <= t1 (<= 63), one per lane (idle
-// lanes: v = -1, d = 0). Their edge lists are laid end to end and dealt out
-// to the lanes 32 at a time, so loads stay coalesced within a row and no lane
-// idles while another walks a long row. The owner of edge e is the last lane
-// whose exclusive prefix offset is <= e.
-
-struct SmallSeg {
-  int off;    // exclusive prefix of degrees over the warp
-  int total;  // sum of degrees over the warp
-};
-
-__device__ __forceinline__ SmallSeg small_scan(int d) {
-  const int lane = lane_id();
-  int incl = d;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(FULL, incl, o);
-    if (lane >= o) incl += y;
-  }
-  SmallSeg g;
-  g.off = incl - d;
-  g.total = __shfl_sync(FULL, incl, 31);
-  return g;
-}
-
-__device__ __forceinline__ int small_owner(int off, int e) {
-  int j = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const int cand = j + step;
-    const int oc = __shfl_sync(FULL, off, cand);
-    if (oc <= e) j = cand;
-  }
-  return j;
-}
-
-constexpr int kSmallUnroll = 8;
-
-// First-fit colour of each lane's node into tent[v]. wm: this warp's 64 words.
-__device__ __forceinline__ void small_assign(const Params& p, int v, int s, int d, unsigned* wm) {
-  const int lane = lane_id();
-  const uint64_t pol = l2_keep_policy();
-  const SmallSeg g = small_scan(d);
-  wm[2 * lane] = 0;
-  wm[2 * lane + 1] = 0;
-  __syncwarp();
-  for (int base = 0; base < g.total; base += 32 * kSmallUnroll) {
-    int u[kSmallUnroll], j[kSmallUnroll];
-#pragma unroll
-    for (int q = 0; q < kSmallUnroll; ++q) {
-      const int e = base + q * 32 + lane;
-      const int jj = small_owner(g.off, e);
-      const int sj = __shfl_sync(FULL, s, jj);
-      const int oj = __shfl_sync(FULL, g.off, jj);
-      j[q] = jj;
-      u[q] = e < g.total ? ld_ro(p.col + sj + (e - oj)) : -1;
-    }
-    int cc[kSmallUnroll];
-#pragma unroll
-    for (int q = 0; q < kSmallUnroll; ++q) cc[q] = u[q] >= 0 ? ld_keep(p.color + u[q], pol) : 0;
-#pragma unroll
-    for (int q = 0; q < kSmallUnroll; ++q) {
-      const int c = cc[q];
-      if (c >= 1 && c <= 64) atomicOr(&wm[2 * j[q] + ((c - 1) >> 5)], 1u << ((c - 1) & 31));
-    }
-  }
-  __syncwarp();
-  if (v >= 0) {
-    const unsigned long long m =
-        (unsigned long long)wm[2 * lane] | ((unsigned long long)wm[2 * lane + 1] << 32);
-    p.tent[v] = __ffsll((long long)~m);
-  }
-  __syncwarp();
-}
-
-// Loser flag of each lane's node (t = its tentative colour).
-__device__ __forceinline__ bool small_lose(const Params& p, int v, int s, int d, int t,
-                                           unsigned* wm) {
-  const int lane = lane_id();
-  const uint64_t pol = l2_keep_policy();
-  const SmallSeg g = small_scan(d);
-  wm[lane] = 0;
-  __syncwarp();
-  for (int base = 0; base < g.total; base += 32 * kSmallUnroll) {
-    int u[kSmallUnroll], j[kSmallUnroll];
-#pragma unroll
-    for (int q = 0; q < kSmallUnroll; ++q) {
-      const int e = base + q * 32 + lane;
-      const int jj = small_owner(g.off, e);
-      const int sj = __shfl_sync(FULL, s, jj);
-      const int oj = __shfl_sync(FULL, g.off, jj);
-      const int vj = __shfl_sync(FULL, v, jj);
-      j[q] = jj;
-      const int uu = e < g.total ? ld_ro(p.col + sj + (e - oj)) : INT_MAX;
-      u[q] = uu < vj ? uu : -1;  // only lower-ID neighbours can beat v
-    }
-    int tt[kSmallUnroll];
-#pragma unroll
-    for (int q = 0; q < kSmallUnroll; ++q) tt[q] = u[q] >= 0 ? ld_keep(p.tent + u[q], pol) : 0;
-#pragma unroll
-    for (int q = 0; q < kSmallUnroll; ++q) {
-      const int tj = __shfl_sync(FULL, t, j[q]);
-      if (u[q] >= 0 && tt[q] == tj) wm[j[q]] = 1u;
-    }
-  }
-  __syncwarp();
-  const bool lose = wm[lane] != 0;
-  __syncwarp();
-  return lose;
-}
-
-// -------------------------------------------------------- high-degree nodes --
-
-// First zero bit among 64 words read by the whole warp through get(i) for
-// i < nw: returns 32 * word + bit + 1 (a colour), or 0 when all are full.
-template <class Get>
-__device__ __forceinline__ int first_free_64(int nw, Get get) {
-  const int lane = lane_id();
-  const unsigned w0 = lane < nw ? get(lane) : FULL;
-  const unsigned w1 = lane + 32 < nw ? get(lane + 32) : FULL;
-  const unsigned b0 = __ballot_sync(FULL, w0 != FULL);
-  const unsigned b1 = __ballot_sync(FULL, w1 != FULL);
-  if (b0) {
-    const int fl = __ffs(b0) - 1;
-    return 32 * fl + __ffs(~__shfl_sync(FULL, w0, fl));
-  }
-  if (b1) {
-    const int fl = __ffs(b1) - 1;
-    return 32 * (32 + fl) + __ffs(~__shfl_sync(FULL, w1, fl));
-  }
-  return 0;
-}
-
-constexpr int kGather = 8;             // neighbour entries per lane per window
-constexpr int kWindow = 32 * kGather;  // neighbour entries per warp per window
-
-// One window of the neighbour array: the kWindow entries at absolute index
-// a + i (a a multiple of 4), lane l holding entries 4l..4l+3 and
-// 128+4l..128+4l+3, read as int4 where the array is 16-byte aligned and the
-// four entries all lie in [lo, hi); entries outside [lo, hi) read `none`.
-__device__ __forceinline__ void load_window(const Params& p, int64_t a, int64_t lo, int64_t hi,
-                                            int none, int (&u)[kGather]) {
-  const int lane = lane_id();
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int64_t q = a + 128 * h + 4 * lane;
-    if (p.col_vec && q >= lo && q + 3 < hi) {
-      const int4 x = __ldg(reinterpret_cast<const int4*>(p.col + q));
-      u[4 * h + 0] = x.x;
-      u[4 * h + 1] = x.y;
-      u[4 * h + 2] = x.z;
-      u[4 * h + 3] = x.w;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        u[4 * h + j] = (q + j >= lo && q + j < hi) ? ld_ro(p.col + q + j) : none;
-    }
-  }
-}
-
-// Asks L2 to fetch neighbour entries [lo, hi) ahead of their use (one lane).
-__device__ __forceinline__ void prefetch_l2(const Params& p, int64_t lo, int64_t hi) {
-  if (!p.col_vec) return;
-  const int64_t a = lo & ~int64_t(3), z = hi & ~int64_t(3);  // 16-byte aligned, inside the array
-  if (z <= a) return;
-  const int64_t bytes = (z - a) * 4;
-  const unsigned sz = (unsigned)(bytes < (1 << 20) ? bytes : (1 << 20));
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p.col + a), "r"(sz) : "memory");
-}
-
-// Colours of neighbours k in [b, e) of row s, shifted by -wbase, into the
-// lane-private mask (1..32) and the warp's bitmap wb (33..lim). The next
-// window's entries are loaded while the current window's colours are
-// gathered.
-__device__ __forceinline__ unsigned gather_colours(const Params& p, int64_t s, int b, int e,
-                                                   int wbase, int lim, unsigned* wb) {
-  const uint64_t pol = l2_keep_policy();
-  const int64_t lo = s + b, hi = s + e;
-  int64_t a = lo & ~int64_t(3);
-  int u[kGather];
-  load_window(p, a, lo, hi, -1, u);
-  unsigned pm = 0;
-  for (; a < hi; a += kWindow) {
-    int un[kGather];
-    const bool more = a + kWindow < hi;
-    if (more) load_window(p, a + kWindow, lo, hi, -1, un);
-    int cc[kGather];
-#pragma unroll
-    for (int q = 0; q < kGather; ++q) cc[q] = u[q] >= 0 ? ld_keep(p.color + u[q], pol) : 0;
-#pragma unroll
-    for (int q = 0; q < kGather; ++q) {
-      const int c = cc[q] - wbase;
-      if (c >= 1 && c <= 32)
-        pm |= 1u << (c - 1);
-      else if (c > 32 && c <= lim)
-        atomicOr(&wb[(c - 1) >> 5], 1u << ((c - 1) & 31));
-    }
-    if (more) {
-#pragma unroll
-      for (int q = 0; q < kGather; ++q) u[q] = un[q];
-    }
-  }
-  __syncwarp();
-  return __reduce_or_sync(FULL, pm);
-}
-
-// A whole node by one warp in windows of 32 * kGWords colours: used when the
-// colour bound of a node exceeds the merge bitmap (more than 2048 colours).
-__device__ int item_assign_windowed(const Params& p, unsigned* wb, int s, int d, int lim) {
-  const int lane = lane_id();
-  for (int wbase = 0;; wbase += 32 * kGWords) {
-    const int wcols = min(lim - wbase, 32 * kGWords);
-    if (wcols <= 0) {  // unreachable for a valid graph: some colour <= lim is free
-      if (lane == 0) atomicCAS(&p.ctrl->status, 0, IPGC_ERR_INVALID);
-      return lim;
-    }
-    const int nw = (wcols + 31) >> 5;
-    const unsigned pm = gather_colours(p, s, 0, d, wbase, wcols, wb);
-    const int t = first_free_64(nw, [&](int i) { return i == 0 ? (pm | wb[0]) : wb[i]; });
-    __syncwarp();
-    wb[lane] = 0;
-    wb[lane + 32] = 0;
-    __syncwarp();
-    if (t > 0) return wbase + t;
-  }
-}
-
-// Assignment step for work item (v, c) of a node with nch items.
-__device__ __forceinline__ void item_assign(const Params& p, unsigned* wb, int v, int s, int d,
-                                            int c, int nch, int gslot, int maxc) {
-  const int lane = lane_id();
-  const int lim = min(d, maxc) + 1;  // tent[v] <= d + 1 and <= maxc + 1
-  if (lim > 32 * kGWords) {
-    if (c == 0) {
-      const int t = item_assign_windowed(p, wb, s, d, lim);
-      if (lane == 0) p.tent[v] = t;
-    }
-    return;
-  }
-  const int nw = (lim + 31) >> 5;
-  const int b = c * p.chunk, e = min(d, b + p.chunk);
-  const unsigned pm = gather_colours(p, s, b, e, 0, lim, wb);
-  if (nch == 1) {
-    const int t = first_free_64(nw, [&](int i) { return i == 0 ? (pm | wb[0]) : wb[i]; });
-    if (lane == 0) p.tent[v] = t;
-    __syncwarp();
-    wb[lane] = 0;
-    wb[lane + 32] = 0;
-    __syncwarp();
-    return;
-  }
-  uint32_t* g = p.gbits + (size_t)gslot * kGWords;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int i = lane + 32 * h;
-    if (i < nw) {
-      const unsigned w = (i == 0 ? pm : 0u) | wb[i];
-      if (w) atomicOr(&g[i], w);
-    }
-  }
-  __syncwarp();
-  wb[lane] = 0;
-  wb[lane + 32] = 0;
-  __threadfence();
-  __syncwarp();
-  int last = 0;
-  if (lane == 0) last = atomicAdd(&p.done_a[gslot], 1) == nch - 1;
-  last = __shfl_sync(FULL, last, 0);
-  if (last) {  // every other item of v has merged its bits
-    __threadfence();
-    const int t = first_free_64(nw, [&](int i) { return atomicExch(&g[i], 0u); });
-    if (lane == 0) {
-      p.tent[v] = t;
-      p.done_a[gslot] = 0;
-    }
-  }
-}
-
-// Conflict step for work item (v, c); the warp that finishes v's last item
-// commits v or pushes its items to the next worklist.
-__device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, int v, int s, int d,
-                                            int c, int nch, int gslot, int nxt, PhaseAcc& acc,
-                                            int round) {
-  const int lane = lane_id();
-  const uint64_t pol = l2_keep_policy();
-  const int t = ld_cg(p.tent + v);
-  const int b = c * p.chunk, e = min(d, b + p.chunk);
-  const int64_t lo = (int64_t)s + b, hi = (int64_t)s + e;
-  bool hit = false;
-  {
-    int64_t a = lo & ~int64_t(3);
-    int u[kGather];
-    load_window(p, a, lo, hi, -1, u);
-    for (; a < hi; a += kWindow) {
-      int un[kGather];
-      const bool more = a + kWindow < hi;
-      if (more) load_window(p, a + kWindow, lo, hi, -1, un);
-      int tt[kGather];
-#pragma unroll
-      for (int q = 0; q < kGather; ++q)
-        tt[q] = (u[q] >= 0 && u[q] < v) ? ld_keep(p.tent + u[q], pol) : 0;
-      bool passed = false;
-#pragma unroll
-      for (int q = 0; q < kGather; ++q) {
-        hit |= (u[q] >= 0 && u[q] < v && tt[q] == t);
-        passed |= u[q] >= v;
-      }
-      if (__any_sync(FULL, hit)) break;
-      if (__any_sync(FULL, passed)) break;  // sorted rows: no lower ID follows
-      if (more) {
-#pragma unroll
-        for (int q = 0; q < kGather; ++q) u[q] = un[q];
-      }
-    }
-  }
-  hit = __any_sync(FULL, hit);
-  int finisher = 1, lose = hit;
-  if (nch > 1) {
-    if (lane == 0) {
-      if (hit) atomicOr(&p.flag[gslot], 1);
-      __threadfence();
-      finisher = atomicAdd(&p.done_d[gslot], 1) == nch - 1;
-      lose = 0;
-      if (finisher) {
-        __threadfence();
-        lose = atomicExch(&p.flag[gslot], 0) != 0;
-        p.done_d[gslot] = 0;
-      }
-    }
-    finisher = __shfl_sync(FULL, finisher, 0);
-    lose = __shfl_sync(FULL, lose, 0);
-  }
-  items_push(stage, v, (finisher && lose && lane == 0) ? nch : 0, gslot, p.items[nxt],
-             &p.ctrl->icnt[nxt]);
-  if (finisher && lane == 0) {
-    if (lose) {
-      acc.nbig += 1;
-      acc.dsum += (unsigned long long)d;
-    } else {
-      p.color[v] = t;
-      acc.maxc = max(acc.maxc, t);
-      if (p.fin) p.fin[v] = round;
-    }
-  }
-}
-
-// ------------------------------------------------------------ work walkers --
-//
-// Both walkers hand a warp its share of the work in a fixed stride and load
-// the next two shares' records (and the next share's row offsets) before
-// working on the current one, so their latency overlaps the gathers.
-
-// Work items k = start, start + stride, ... < count: calls
-// f(v, chunk, gslot, nch, s, d) for every item whose node is active.
-template <class F>
-__device__ __forceinline__ void for_items(const Params& p, const int4* items, int64_t count,
-                                          bool topo, int64_t start, int64_t stride, F f) {
-  if (start >= count) return;
-  const int4 none = make_int4(0, 0, -1, 0);
-  int4 A = ld_cg4(items + start);
-  int4 B = start + stride < count ? ld_cg4(items + start + stride) : none;
-  int sA = ld_ro(p.rowptr + A.x), eA = ld_ro(p.rowptr + A.x + 1);
-  int cA = topo ? ld_cg(p.color + A.x) : 0;
-  for (int64_t k = start; k < count; k += stride) {
-    int sB = 0, eB = 0, cB = 0;
-    if (k + stride < count) {
-      sB = ld_ro(p.rowptr + B.x);
-      eB = ld_ro(p.rowptr + B.x + 1);
-      if (topo) cB = ld_cg(p.color + B.x);
-    }
-    const int4 C = k + 2 * stride < count ? ld_cg4(items + k + 2 * stride) : none;
-    if (cA == 0) f(A.x, A.y, A.z, A.w, sA, eA - sA);
-    if (k + stride < count && cB == 0 && lane_id() == 0) {  // B's neighbours, into L2
-      const int64_t lo = (int64_t)sB + (int64_t)B.y * p.chunk;
-      prefetch_l2(p, lo, min((int64_t)eB, lo + p.chunk));
-    }
-    A = B;
-    sA = sB;
-    eA = eB;
-    cA = cB;
-    B = C;
-  }
-}
-
-// Low-degree nodes, 32 per share: the worklist entries [base, base + 32) or,
-// topology-driven, node IDs [base, base + 32) of degree <= t1 and colour 0.
-// Calls f(v, s, d, t) per share for all lanes (v = -1, d = 0 on idle lanes;
-// t = tent[v] when WithTent).
-template <bool WithTent, class F>
-__device__ __forceinline__ void for_small(const Params& p, const int32_t* list, int64_t span,
-                                          bool topo, int64_t start, int64_t stride, F f) {
-  if (start >= span) return;
-  const int lane = lane_id();
-  auto node_at = [&](int64_t i) -> int {
-    return i < span ? (topo ? (int)i : ld_cg(list + i)) : -1;
-  };
-  int vA = node_at(start + lane);
-  int vB = node_at(start + stride + lane);
-  int sA = 0, eA = 0, cA = 0, tA = 0;
-  if (vA >= 0) {
-    sA = ld_ro(p.rowptr + vA);
-    eA = ld_ro(p.rowptr + vA + 1);
-    if (topo) cA = ld_cg(p.color + vA);
-    if (WithTent) tA = ld_cg(p.tent + vA);
-  }
-  for (int64_t base = start; base < span; base += stride) {
-    int sB = 0, eB = 0, cB = 0, tB = 0;
-    if (vB >= 0) {
-      sB = ld_ro(p.rowptr + vB);
-      eB = ld_ro(p.rowptr + vB + 1);
-      if (topo) cB = ld_cg(p.color + vB);
-      if (WithTent) tB = ld_cg(p.tent + vB);
-    }
-    const int vC = node_at(base + 2 * stride + lane);
-    int v = vA, d = eA - sA;
-    if (v >= 0 && topo && (d > p.t1 || cA != 0)) v = -1;
-    if (v < 0) d = 0;
-    f(v, sA, d, tA);
-    vA = vB;
-    sA = sB;
-    eA = eB;
-    cA = cB;
-    tA = tB;
-    vB = vC;
-  }
-}
-
-// ------------------------------------------------------------------ phases --
-
-struct RoundView {
-  int round;   // 1-based round number
-  int par;     // worklist parity read this round
-  int mode;    // MODE_TOPO or MODE_DATA
-  int nsmall;  // low-degree nodes in the worklist
-  int nbig;    // high-degree nodes in the worklist
-  int icnt;    // their work items
-  int nistat;  // work items of every high-degree node
-  int maxc;    // largest committed colour at round start
-};
-
-__device__ __forceinline__ RoundView read_round(const Params& p, int r) {
-  RoundView rv;
-  rv.round = r;
-  rv.par = r & 1;
-  rv.nsmall = ld_cg(&p.ctrl->cnt[rv.par][B_SMALL]);
-  rv.nbig = ld_cg(&p.ctrl->cnt[rv.par][B_BIG]);
-  rv.icnt = ld_cg(&p.ctrl->icnt[rv.par]);
-  rv.nistat = ld_cg(&p.ctrl->nistat);
-  rv.maxc = ld_cg(&p.ctrl->maxc);
-  rv.mode = MODE_DATA;
-  return rv;
-}
-
-__device__ __forceinline__ int decide_mode(const Params& p, int64_t total) {
-  if (p.policy == IPGC_MODE_TOPO) return MODE_TOPO;
-  if (p.policy == IPGC_MODE_DATA) return MODE_DATA;
-  return total > p.H ? MODE_TOPO : MODE_DATA;
-}
-
-// Bookkeeping by CTA 0 at the start of round r (after the previous barrier):
-// clear the counters this round pushes into and count the round.
-__device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv, int r,
-                                            int64_t total) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  Ctrl* c = p.ctrl;
-  const int nxt = rv.par ^ 1;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) c->cnt[nxt][k] = 0;
-  c->icnt[nxt] = 0;
-  c->dsum[nxt] = 0;
-  c->rounds = r;
-  if (rv.mode == MODE_TOPO)
-    c->rounds_topo += 1;
-  else
-    c->rounds_data += 1;
-  c->last_mode = rv.mode;
-  const unsigned long long ds = __ldcg(&c->dsum[rv.par]);
-  c->edges += ds;
-  if (p.trace && r <= p.trace_cap) {
-    ipgc_trace_rec& tr = p.trace[r - 1];
-    tr.round = r;
-    tr.mode = rv.mode;
-    tr.wl_size = total;
-    tr.deg_sum = (int64_t)ds;
-    tr.max_color = rv.maxc;
-    tr.shortcut = 0;
-    tr.t_begin = gtime();
-  }
-  __threadfence();
-}
-
-template <int BS>
-__device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv) {
-  const int warp = threadIdx.x >> 5, lane = lane_id();
-  const int gwarp = blockIdx.x * (BS / 32) + warp, nwarps = gridDim.x * (BS / 32);
-  const bool topo = rv.mode == MODE_TOPO;
-  {  // high-degree work items: one warp each
-    const int4* items = topo ? p.istat : p.items[rv.par];
-    const int count = topo ? rv.nistat : rv.icnt;
-    unsigned* wb = sm.wbits[warp];
-    for_items(p, items, count, topo, gwarp, nwarps,
-              [&](int v, int c, int gslot, int nch, int s, int d) {
-                item_assign(p, wb, v, s, d, c, nch, gslot, rv.maxc);
-              });
-  }
-  {  // low-degree nodes: 32 per warp
-    unsigned* wm = sm.small_w[warp];
-    const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
-    for_small<false>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
-                     [&](int v, int s, int d, int) { small_assign(p, v, s, d, wm); });
-  }
-  (void)lane;
-}
-
-template <int BS>
-__device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv, PhaseAcc& acc) {
-  const int warp = threadIdx.x >> 5, lane = lane_id();
-  const int gwarp = blockIdx.x * (BS / 32) + warp, nwarps = gridDim.x * (BS / 32);
-  const bool topo = rv.mode == MODE_TOPO;
-  const int nxt = rv.par ^ 1;
-  Ctrl* c = p.ctrl;
-  {
-    const int4* items = topo ? p.istat : p.items[rv.par];
-    const int count = topo ? rv.nistat : rv.icnt;
-    ItemStage stage{sm.stage_i[warp], 0};
-    for_items(p, items, count, topo, gwarp, nwarps,
-              [&](int v, int cidx, int gslot, int nch, int s, int d) {
-                item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, rv.round);
-              });
-    items_flush(stage, p.items[nxt], &c->icnt[nxt]);
-  }
-  {
-    unsigned* wm = sm.small_w[warp];
-    WarpStage sg{sm.stage_s[warp], 0};
-    const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
-    for_small<true>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
-                    [&](int v, int s, int d, int t) {
-                      const bool lose = small_lose(p, v, s, d, t, wm);
-                      stage_push(sg, kStageSmall, v >= 0 && lose, v, p.wl[nxt],
-                                 &c->cnt[nxt][B_SMALL]);
-                      if (v >= 0) {
-                        if (lose) {
-                          acc.dsum += (unsigned long long)d;
-                        } else {
-                          p.color[v] = t;
-                          acc.maxc = max(acc.maxc, t);
-                          if (p.fin) p.fin[v] = rv.round;
-                        }
-                      }
-                    });
-    stage_flush(sg, p.wl[nxt], &c->cnt[nxt][B_SMALL]);
-  }
-  (void)lane;
-}
-
-__device__ __forceinline__ void trace_round1(const Params& p, uint64_t t0) {
-  Ctrl* c = p.ctrl;
-  c->rounds = 1;
-  c->rounds_topo = 1;
-  c->last_mode = MODE_TOPO;
-  c->edges = (unsigned long long)p.nnz;
-  if (p.trace && p.trace_cap >= 1) {
-    const uint64_t t1 = gtime();
-    ipgc_trace_rec& tr = p.trace[0];
-    tr.round = 1;
-    tr.mode = MODE_TOPO;
-    tr.wl_size = p.n;
-    tr.deg_sum = p.nnz;
-    tr.max_color = 0;
-    tr.shortcut = 1;
-    tr.t_begin = t0;
-    tr.t_assign = t0;
-    tr.t_detect = t1;
-  }
-}
 
 // ------------------------------------------------------- persistent kernel --
 
@@ -758,41 +40,7 @@ template <int BS>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(Params p) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
-  Ctrl* c = p.ctrl;
-  const uint64_t t0 = gtime();
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->t_start = t0;
-  {
-    PhaseAcc acc;
-    round1<BS>(p, sm, acc);
-    phase_commit<BS>(p, sm, acc, 0);
-  }
-  if (!grid_barrier(c, p.timeout_ns, p.bar_extra)) goto done;
-  if (blockIdx.x == 0 && threadIdx.x == 0) trace_round1(p, t0);
-  for (int r = 2;; ++r) {
-    RoundView rv = read_round(p, r);
-    const int64_t total = (int64_t)rv.nsmall + rv.nbig;
-    if (total == 0) break;
-    if (r > p.max_rounds) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&c->status, 0, IPGC_ERR_NO_CONVERGE);
-      break;
-    }
-    rv.mode = decide_mode(p, total);
-    round_begin(p, rv, r, total);
-    assign_phase<BS>(p, sm, rv);
-    if (!grid_barrier(c, p.timeout_ns, p.bar_extra)) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace && r <= p.trace_cap)
-      p.trace[r - 1].t_assign = gtime();
-    {
-      PhaseAcc acc;
-      detect_phase<BS>(p, sm, rv, acc);
-      phase_commit<BS>(p, sm, acc, rv.par ^ 1);
-    }
-    if (!grid_barrier(c, p.timeout_ns, p.bar_extra)) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace && r <= p.trace_cap)
-      p.trace[r - 1].t_detect = gtime();
-  }
-done:
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->t_end = gtime();
+  color_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // ------------------------------------------------------ host-loop kernels --
@@ -803,7 +51,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) round1_kernel(Params p) {
   const uint64_t t0 = gtime();
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctrl->t_start = t0;
   PhaseAcc acc;
-  round1<BS>(p, sm, acc);
+  round1<BS>(p, sm, acc, Team{(int)blockIdx.x, (int)gridDim.x});
   phase_commit<BS>(p, sm, acc, 0);
   if (blockIdx.x == 0 && threadIdx.x == 0) trace_round1(p, t0);
 }
@@ -818,8 +66,9 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) assign_kernel(Params p, in
   RoundView rv = read_round(p, r);
   rv.mode = mode;
   const int64_t total = (int64_t)rv.nsmall + rv.nbig;
-  round_begin(p, rv, r, total);
-  assign_phase<BS>(p, sm, rv);
+  const Team tm{(int)blockIdx.x, (int)gridDim.x};
+  round_begin(p, rv, r, total, tm);
+  assign_phase<BS>(p, sm, rv, tm);
 }
 
 template <int BS>
@@ -831,7 +80,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) detect_kernel(Params p, in
   RoundView rv = read_round(p, r);
   rv.mode = mode;
   PhaseAcc acc;
-  detect_phase<BS>(p, sm, rv, acc);
+  detect_phase<BS>(p, sm, rv, acc, Team{(int)blockIdx.x, (int)gridDim.x});
   phase_commit<BS>(p, sm, acc, rv.par ^ 1);
 }
 
@@ -885,15 +134,6 @@ __global__ void validate_kernel(const int32_t* __restrict__ rowptr, const int32_
 }
 
 // ------------------------------------------------------------ host launch --
-
-template <class F>
-cudaError_t with_block(int bs, F f) {
-  switch (bs) {
-    case 256: return f(std::integral_constant<int, 256>());
-    case 512: return f(std::integral_constant<int, 512>());
-    default: return cudaErrorInvalidValue;
-  }
-}
 
 cudaError_t occupancy_persistent(int bs, int* blocks_per_sm) {
   return with_block(bs, [&](auto B) {

@@ -106,10 +106,19 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ int bucket_of(int d, int t1) { return d <= t1 ? B_SMALL : B_BIG; }
 
-// Grid-wide barrier for a cooperative launch, bounded by timeout_ns: a CTA
-// that waits longer records IPGC_ERR_TIMEOUT and leaves the barrier. Returns
-// false when the launch must stop (timeout here or an error elsewhere).
-__device__ __forceinline__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, uint32_t extra = 0) {
+// The CTAs that colour one graph together: this CTA's rank and their number.
+struct Team {
+  int cta;
+  int ncta;
+};
+
+// Barrier of a team of co-resident CTAs (a cooperative launch guarantees
+// residency), bounded by timeout_ns: a CTA that waits longer records
+// IPGC_ERR_TIMEOUT and leaves the barrier. Returns false when the team must
+// stop (timeout here or an error recorded elsewhere). The counters live in
+// the graph's control block. `extra` phantom CTAs never arrive (tests).
+__device__ __forceinline__ bool team_barrier(Ctrl* c, int ncta, uint64_t timeout_ns,
+                                             uint32_t extra = 0) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -117,7 +126,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* c, uint64_t timeout_ns, uint3
     const uint32_t gen = *genp;
     __threadfence();
     const uint32_t arrived = atomicAdd(&c->bar_count, 1u);
-    if (arrived == gridDim.x + extra - 1) {
+    if (arrived == (uint32_t)ncta + extra - 1) {
       c->bar_count = 0;
       __threadfence();
       atomicAdd(&c->bar_gen, 1u);

@@ -1,0 +1,132 @@
+"""Batched colouring: every graph of a batch gets, bit for bit, the colouring
+the CPU oracle gives it alone, whatever the team split, team size, mode or
+block size (the schedule must never change a colour)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_01478_gb300 import graphgen
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(graphs):
+    """Concatenate (rowptr, col) pairs into the batched layout."""
+    node_off = np.zeros(len(graphs) + 1, np.int64)
+    edge_off = np.zeros(len(graphs) + 1, np.int64)
+    rps, cls = [], []
+    for g, (rp, cl) in enumerate(graphs):
+        node_off[g + 1] = node_off[g] + rp.size - 1
+        edge_off[g + 1] = edge_off[g] + cl.size
+        rps.append(rp)
+        cls.append(cl)
+    return dict(
+        node_off=node_off,
+        edge_off=edge_off,
+        rowptr_cat=np.concatenate(rps).astype(np.int32),
+        col_cat=np.concatenate(cls).astype(np.int32) if edge_off[-1] else np.zeros(0, np.int32),
+    )
+
+
+def run_batch(ctx, bt, **kw):
+    import torch
+
+    from paper_1912_01478_gb300 import batched
+
+    drp = torch.from_numpy(bt["rowptr_cat"]).cuda()
+    dcl = torch.from_numpy(bt["col_cat"]).cuda()
+    colors, st = batched.color_batched(ctx, bt["node_off"], bt["edge_off"], drp, dcl,
+                                       opts=batched.options(**kw))
+    return colors.cpu().numpy(), st
+
+
+def check_against_oracle(bt, colors, st, refs=None):
+    no = bt["node_off"]
+    G = no.size - 1
+    for g in range(G):
+        rp, cl = graphgen.batch_graph(bt, g)
+        ref = refs[g] if refs is not None else oracle.color(rp, cl, trace=False)
+        got = colors[no[g]:no[g + 1]]
+        assert np.array_equal(got, ref.colors), g
+        assert st["rounds"][g] == ref.rounds and st["num_colors"][g] == ref.num_colors, g
+        assert st["error"][g] == 0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1912_01478_gb300 import _build, ipgc
+
+    _build.build()
+    return ipgc.Context(0)
+
+
+@pytest.fixture(scope="module")
+def mixed_batch():
+    bt = graphgen.batch(48, seed=4, nmin=100, nmax=40_000)
+    refs = []
+    for g in range(48):
+        rp, cl = graphgen.batch_graph(bt, g)
+        refs.append(oracle.color(rp, cl, trace=False))
+    return bt, refs
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [
+        dict(),
+        dict(team_min_nnz=0),                    # every graph on a team of 8
+        dict(team_min_nnz=0, team_size=2),
+        dict(team_min_nnz=50_000, team_size=16),
+        dict(team_min_nnz=1 << 40),              # every graph on one CTA
+        dict(mode="data"),
+        dict(mode="topo", team_min_nnz=100_000),
+        dict(block_size=512, chunk=256, t1=8),
+    ],
+)
+def test_batch_matches_oracle(ctx, mixed_batch, kw):
+    bt, refs = mixed_batch
+    colors, st = run_batch(ctx, bt, **kw)
+    check_against_oracle(bt, colors, st, refs)
+
+
+def test_degenerate_graphs_in_a_batch(ctx):
+    import itertools
+
+    edgeless = graphgen.from_edges(5, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    one = graphgen.from_edges(1, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    empty = (np.zeros(1, np.int32), np.zeros(0, np.int32))
+    k = 70
+    e = np.array(list(itertools.combinations(range(k), 2)), np.int32)
+    clique = graphgen.from_edges(k, e[:, 0], e[:, 1])
+    star = graphgen.from_edges(3000, np.zeros(2999, np.int32), np.arange(1, 3000, dtype=np.int32))
+    graphs = [edgeless, empty, one, clique, graphgen.rmat(12, 8, seed=5), empty, star]
+    bt = make_batch(graphs)
+    colors, st = run_batch(ctx, bt, team_min_nnz=4000)
+    check_against_oracle(bt, colors, st)
+    assert st["rounds"][1] == 0 and st["rounds"][5] == 0
+
+
+def test_batch_equals_single_graph_calls(ctx):
+    import torch
+
+    bt = graphgen.batch(16, seed=7, nmin=2_000, nmax=60_000)
+    colors, st = run_batch(ctx, bt, team_min_nnz=100_000)
+    no = bt["node_off"]
+    for g in range(16):
+        rp, cl = graphgen.batch_graph(bt, g)
+        one, st1 = ctx.color(torch.from_numpy(np.ascontiguousarray(rp)).cuda(),
+                             torch.from_numpy(np.ascontiguousarray(cl)).cuda())
+        assert np.array_equal(one.cpu().numpy(), colors[no[g]:no[g + 1]])
+        assert st1.rounds == st["rounds"][g]
+
+
+def test_batch_validation(ctx):
+    from paper_1912_01478_gb300 import ipgc
+
+    rp, cl = graphgen.er(300, 900, seed=3)
+    bad = cl.copy()
+    bad[0] = 10_000
+    bt = make_batch([graphgen.er(200, 500, seed=2), (rp, bad)])
+    with pytest.raises(ipgc.IpgcError) as ei:
+        run_batch(ctx, bt, validate=True)
+    assert ei.value.code == ipgc.IPGC_ERR_INVALID
