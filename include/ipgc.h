@@ -237,6 +237,26 @@ IPGC_API int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t
                                 void* stream);
 
 /*
+ * Schedule autotuners. The schedule (t1, chunk, block_size and,
+ * for batches, team_size and team_min_nnz) changes speed only, never a
+ * colour. Starting from *opt, each knob in turn is set to every candidate
+ * value, the colouring is timed (best of `reps`, CUDA events on `stream`) and
+ * the fastest value is kept; *opt receives the result and *best_ms (may be
+ * NULL) its time. ipgc_autotune times ipgc_color_ex on the given graph
+ * (colors_scratch: device int32[n], overwritten); ipgc_batched_autotune times
+ * ipgc_color_batched on the batch's first sample_graphs graphs (0 = all),
+ * writing their colours to colors_cat. Errors as the timed calls.
+ */
+IPGC_API int ipgc_autotune(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
+                           int64_t nnz, int32_t* colors_scratch, int32_t reps, ipgc_options* opt,
+                           float* best_ms, void* stream);
+IPGC_API int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_off,
+                                   const int64_t* edge_off, const int32_t* rowptr_cat,
+                                   const int32_t* col_cat, int32_t* colors_cat,
+                                   int32_t sample_graphs, int32_t reps, ipgc_batch_options* opt,
+                                   float* best_ms, void* stream);
+
+/*
  * Colour one graph without allocating anything (the paper has no counterpart;
  * this exists for callers that cannot allocate device memory when they need
  * a colouring, e.g. code running inside an allocator or memory-pool callback,

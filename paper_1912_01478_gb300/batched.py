@@ -25,7 +25,34 @@ SIGNATURES = {
         [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.POINTER(ipgc.Stats),
          ctypes.POINTER(BatchOptions), _P],
     ),
+    "ipgc_batched_autotune": (
+        ctypes.c_int,
+        [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+         ctypes.POINTER(BatchOptions), ctypes.POINTER(ctypes.c_float), _P],
+    ),
 }
+
+
+def autotune(ctx: "ipgc.Context", node_off, edge_off, rowptr_cat, col_cat, colors_cat,
+             opts: BatchOptions | None = None, sample_graphs: int = 0, reps: int = 2, stream=None):
+    """Run the native schedule autotuner; returns (BatchOptions, best ms)."""
+    node_off = np.ascontiguousarray(node_off, dtype=np.int64)
+    edge_off = np.ascontiguousarray(edge_off, dtype=np.int64)
+    o = opts if opts is not None else options()
+    best = ctypes.c_float(0)
+    rc = lib().ipgc_batched_autotune(
+        ctx.handle, node_off.size - 1, node_off.ctypes.data, edge_off.ctypes.data,
+        rowptr_cat.data_ptr(), col_cat.data_ptr(), colors_cat.data_ptr(), sample_graphs, reps,
+        ctypes.byref(o), ctypes.byref(best), ipgc._stream_handle(stream) or None,
+    )
+    if rc != ipgc.IPGC_OK:
+        raise ipgc.IpgcError(rc, "ipgc_batched_autotune")
+    return o, best.value
+
+
+def describe(o: BatchOptions) -> dict:
+    return dict(t1=o.base.t1, chunk=o.base.chunk, block_size=o.base.block_size,
+                team_size=o.team_size, team_min_nnz=int(o.team_min_nnz), mode=o.base.mode)
 
 _bound = False
 

@@ -1,0 +1,148 @@
+// Schedule autotuner for the single-graph and batched colourings.
+//
+// The schedule (degree split t1, work-item size, CTA size, team size and the
+// size from which a graph of a batch gets a team) changes only speed, never a
+// colour, so it can be chosen by measurement. The tuner runs a coordinate
+// descent from the caller's options: for each knob in turn it times every
+// candidate value with the others fixed (best of `reps` launches, CUDA events
+// on the caller's stream) and keeps the fastest. The batched tuner times the
+// batch's first `sample_graphs` graphs, a contiguous prefix that is itself a
+// valid batch.
+#include <cfloat>
+#include <cstring>
+#include <vector>
+
+#include "ipgc_internal.h"
+
+namespace {
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  bool ok = false;
+  Timer() { ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess; }
+  ~Timer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+template <class Run>
+int time_best(Run run, cudaStream_t s, int reps, float* best) {
+  Timer t;
+  if (!t.ok) return IPGC_ERR_CUDA;
+  *best = FLT_MAX;
+  for (int r = 0; r < reps; ++r) {
+    if (cudaEventRecord(t.a, s) != cudaSuccess) return IPGC_ERR_CUDA;
+    const int rc = run();
+    if (rc != IPGC_OK) return rc;
+    if (cudaEventRecord(t.b, s) != cudaSuccess || cudaEventSynchronize(t.b) != cudaSuccess)
+      return IPGC_ERR_CUDA;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess) return IPGC_ERR_CUDA;
+    if (ms < *best) *best = ms;
+  }
+  return IPGC_OK;
+}
+
+// One knob: a setter and its candidate values.
+template <class Opt>
+struct Knob {
+  void (*set)(Opt&, int64_t);
+  std::vector<int64_t> values;
+};
+
+template <class Opt, class Run>
+int descend(Opt* opt, const std::vector<Knob<Opt>>& knobs, Run run, cudaStream_t s, int reps,
+            float* best_ms) {
+  Opt best = *opt;
+  float best_t = FLT_MAX;
+  int rc = time_best([&] { return run(best); }, s, reps, &best_t);
+  if (rc != IPGC_OK) return rc;
+  for (const Knob<Opt>& k : knobs) {
+    Opt here = best;
+    for (int64_t v : k.values) {
+      Opt cand = best;
+      k.set(cand, v);
+      float t = 0;
+      rc = time_best([&] { return run(cand); }, s, reps, &t);
+      if (rc != IPGC_OK) return rc;
+      if (t < best_t) {
+        best_t = t;
+        here = cand;
+      }
+    }
+    best = here;
+  }
+  *opt = best;
+  if (best_ms) *best_ms = best_t;
+  return IPGC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ipgc_autotune(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
+                  int32_t* colors_scratch, int32_t reps, ipgc_options* opt, float* best_ms,
+                  void* stream) {
+  if (!ctx || !opt || reps < 1) return IPGC_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  ipgc_options base = *opt;
+  base.validate = 0;
+  base.trace = nullptr;
+  base.fin_round = nullptr;
+  base.fault_inject = 0;
+  std::vector<Knob<ipgc_options>> knobs = {
+      {[](ipgc_options& o, int64_t v) { o.chunk = (int32_t)v; }, {256, 512, 1024, 2048, 4096}},
+      {[](ipgc_options& o, int64_t v) { o.t1 = (int32_t)v; }, {8, 16, 24, 40, 63}},
+      {[](ipgc_options& o, int64_t v) { o.block_size = (int32_t)v; }, {256, 512}},
+  };
+  const int rc = descend(
+      &base, knobs,
+      [&](const ipgc_options& o) {
+        return ipgc_color_ex(ctx, rowptr, col, n, nnz, colors_scratch, nullptr, &o, stream);
+      },
+      s, reps, best_ms);
+  if (rc != IPGC_OK) return rc;
+  const int validate = opt->validate;
+  ipgc_trace_rec* trace = opt->trace;
+  int32_t* fin = opt->fin_round;
+  *opt = base;
+  opt->validate = validate;
+  opt->trace = trace;
+  opt->fin_round = fin;
+  return IPGC_OK;
+}
+
+int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_off,
+                          const int64_t* edge_off, const int32_t* rowptr_cat, const int32_t* col_cat,
+                          int32_t* colors_cat, int32_t sample_graphs, int32_t reps,
+                          ipgc_batch_options* opt, float* best_ms, void* stream) {
+  if (!ctx || !opt || reps < 1 || num_graphs < 0 || !node_off || !edge_off) return IPGC_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t G = (sample_graphs > 0 && sample_graphs < num_graphs) ? sample_graphs : num_graphs;
+  ipgc_batch_options base = *opt;
+  const int validate = base.base.validate;
+  base.base.validate = 0;
+  std::vector<Knob<ipgc_batch_options>> knobs = {
+      {[](ipgc_batch_options& o, int64_t v) { o.base.chunk = (int32_t)v; }, {512, 1024, 2048}},
+      {[](ipgc_batch_options& o, int64_t v) { o.base.t1 = (int32_t)v; }, {16, 24, 40, 63}},
+      {[](ipgc_batch_options& o, int64_t v) { o.team_min_nnz = v; },
+       {1 << 16, 1 << 18, 1 << 20, (int64_t)1 << 40}},
+      {[](ipgc_batch_options& o, int64_t v) { o.team_size = (int32_t)v; }, {2, 4, 8, 16}},
+      {[](ipgc_batch_options& o, int64_t v) { o.base.block_size = (int32_t)v; }, {256, 512}},
+  };
+  const int rc = descend(
+      &base, knobs,
+      [&](const ipgc_batch_options& o) {
+        return ipgc_color_batched(ctx, G, node_off, edge_off, rowptr_cat, col_cat, colors_cat,
+                                  nullptr, &o, stream);
+      },
+      s, reps, best_ms);
+  if (rc != IPGC_OK) return rc;
+  base.base.validate = validate;
+  *opt = base;
+  return IPGC_OK;
+}
+
+}  // extern "C"

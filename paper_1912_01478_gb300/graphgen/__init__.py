@@ -203,6 +203,13 @@ def num_threads() -> int:
     return int(_load().gg_num_threads())
 
 
+def batch_workload(num_graphs: int = 4096, seed: int = 4):
+    """The batched workload: num_graphs graphs, n log-uniform in [100, 200000],
+    even index Erdos-Renyi with average degree U(4, 32), odd index RMAT with
+    edge factor 8 (IDs permuted), per-graph seeds derived from `seed`."""
+    return batch(num_graphs, seed=seed, nmin=100, nmax=200_000, deg_lo=4.0, deg_hi=32.0, rmat_ef=8)
+
+
 # Named workloads: the paper-shaped synthetic inputs (sizes as stated).
 def workload(name: str):
     """Return (rowptr, col) for a named single-graph workload."""

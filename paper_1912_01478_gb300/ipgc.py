@@ -133,6 +133,10 @@ SIGNATURES = {
     ),
     "ipgc_validate_csr": (_INT, [_P, _P, _P, _I32, _I64, _INT, _P]),
     "ipgc_color_noalloc": (_INT, [_P, _P, _I32, _I64, _P, ctypes.POINTER(Stats), _P]),
+    "ipgc_autotune": (
+        _INT,
+        [_P, _P, _P, _I32, _I64, _P, _I32, ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_float), _P],
+    ),
 }
 
 

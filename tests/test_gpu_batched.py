@@ -130,3 +130,34 @@ def test_batch_validation(ctx):
     with pytest.raises(ipgc.IpgcError) as ei:
         run_batch(ctx, bt, validate=True)
     assert ei.value.code == ipgc.IPGC_ERR_INVALID
+
+
+def test_autotuners_keep_colours(ctx):
+    import ctypes
+
+    import torch
+
+    from paper_1912_01478_gb300 import batched, ipgc
+
+    bt = graphgen.batch(24, seed=9, nmin=500, nmax=30_000)
+    drp = torch.from_numpy(bt["rowptr_cat"]).cuda()
+    dcl = torch.from_numpy(bt["col_cat"]).cuda()
+    out = torch.empty(int(bt["node_off"][-1]), dtype=torch.int32, device="cuda")
+    o, ms = batched.autotune(ctx, bt["node_off"], bt["edge_off"], drp, dcl, out, sample_graphs=12)
+    assert ms > 0 and o.base.chunk in (512, 1024, 2048) and o.team_size in (2, 4, 8, 16)
+    colors, st = batched.color_batched(ctx, bt["node_off"], bt["edge_off"], drp, dcl, opts=o)
+    check_against_oracle(bt, colors.cpu().numpy(), st)
+    # single-graph tuner
+    rp, cl = graphgen.rmat(14, 16, seed=3)
+    ref = oracle.color(rp, cl, trace=False)
+    g_rp, g_cl = torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda()
+    scratch = torch.empty(rp.size - 1, dtype=torch.int32, device="cuda")
+    opt = ipgc.ColorOptions().to_c()
+    best = ctypes.c_float(0)
+    rc = ipgc.lib().ipgc_autotune(ctx.handle, g_rp.data_ptr(), g_cl.data_ptr(), rp.size - 1, cl.size,
+                                  scratch.data_ptr(), 2, ctypes.byref(opt), ctypes.byref(best), None)
+    assert rc == 0 and best.value > 0 and opt.chunk in (256, 512, 1024, 2048, 4096)
+    st1 = ipgc.Stats()
+    rc = ipgc.lib().ipgc_color_ex(ctx.handle, g_rp.data_ptr(), g_cl.data_ptr(), rp.size - 1, cl.size,
+                                  scratch.data_ptr(), ctypes.byref(st1), ctypes.byref(opt), None)
+    assert rc == 0 and np.array_equal(scratch.cpu().numpy(), ref.colors)
