@@ -96,6 +96,8 @@ typedef struct ipgc_trace_rec {
   int64_t deg_sum;    /* sum of deg(v) over the worklist */
   int32_t max_color;  /* largest committed colour at the start of the round */
   int32_t shortcut;   /* 1 for round 1, whose assignment step is implicit */
+  int32_t wl_small;   /* worklist nodes of degree <= t1 */
+  int32_t reserved;
   uint64_t t_begin;   /* %globaltimer at the start of the round (ns) */
   uint64_t t_assign;  /* ... after the assignment step's grid barrier */
   uint64_t t_detect;  /* ... after the conflict step's grid barrier */
@@ -121,6 +123,10 @@ typedef struct ipgc_options {
   int32_t fault_inject;   /* tests only: 1 = every grid barrier also waits for a CTA that
                              never arrives, so the launch ends with IPGC_ERR_TIMEOUT after
                              timeout_ns (exercises the bounded waits); 0 otherwise */
+  float policy_margin;    /* IPGC_MODE_LEARNED: when the network's probability p of "topology
+                             is faster" has |p - 0.5| < policy_margin, or no network is
+                             loaded, the threshold rule decides; default 0.05 */
+  int32_t reserved2;
 } ipgc_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -235,6 +241,46 @@ IPGC_API int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t
                                 const int32_t* col_cat, int32_t* colors_cat,
                                 ipgc_stats* per_graph_stats, const ipgc_batch_options* opt,
                                 void* stream);
+
+/*
+ * Learned mode switch. A multilayer perceptron 8 -> 16 -> 16 -> 1 (tanh
+ * hidden units, logistic output) gives the probability that the round runs
+ * faster topology-driven than data-driven (Section IV leaves the choice of H
+ * to experiment; Section VII asks for a better rule). Parameters, float32,
+ * IPGC_MLP_PARAMS of them: W1[16][8], b1[16], W2[16][16], b2[16], w3[16], b3.
+ * The 8 inputs of a round are computed from its trace record by
+ * ipgc_policy_features (the colouring kernel computes the same values the
+ * same way when it runs with IPGC_MODE_LEARNED).
+ */
+#define IPGC_MLP_INPUTS 8
+#define IPGC_MLP_HIDDEN 16
+#define IPGC_MLP_PARAMS 433
+
+/* Features of `rounds` trace records (device pointers; feats: float[rounds][8]). */
+IPGC_API int ipgc_policy_features(const ipgc_trace_rec* trace, int32_t rounds, int32_t n,
+                                  int64_t nnz, float* feats, void* stream);
+/* Forward pass: prob[i] = network output for x[i][0..8) (device pointers). */
+IPGC_API int ipgc_mlp_forward(const float* w, const float* x, int32_t n, float* prob, void* stream);
+/*
+ * Loss and gradient of the weighted logistic loss
+ *   L = sum_i wt[i] * (softplus(z_i) - y[i] * z_i) / sum_i wt[i]
+ * over n samples (device pointers; y in {0, 1}, wt >= 0). grad: float[433],
+ * loss: float[1]; scratch: float[434 * n] per-sample terms, summed in a fixed
+ * order (the result does not depend on thread timing).
+ */
+IPGC_API int ipgc_mlp_grad(const float* w, const float* x, const float* y, const float* wt,
+                           int32_t n, float* grad, float* loss, float* scratch, void* stream);
+/*
+ * Full-batch Adam on the device with the kernels above (beta1 0.9, beta2
+ * 0.999, eps 1e-8): `epochs` steps from the weights in w_inout (device
+ * float[433]), updated in place. loss_out (host, may be NULL) receives the
+ * loss before the last step. Scratch comes from the context's workspace.
+ */
+IPGC_API int ipgc_mlp_train(ipgc_ctx* ctx, const float* x, const float* y, const float* wt,
+                            int32_t n, int32_t epochs, float lr, float* w_inout, float* loss_out,
+                            void* stream);
+/* Copy 433 host floats into the context; IPGC_MODE_LEARNED then uses them. len = 0 unloads. */
+IPGC_API int ipgc_policy_load(ipgc_ctx* ctx, const float* w, int32_t len);
 
 /*
  * Schedule autotuners. The schedule (t1, chunk, block_size and,

@@ -1,4 +1,5 @@
 // C ABI of libipgc.so: contexts, workspace, argument checks, drivers.
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -28,6 +29,7 @@ struct ipgc_ctx {
   // learned policy weights
   float* d_mlp = nullptr;
   int32_t mlp_len = 0;
+  std::vector<float> h_mlp;  // host copy (host-loop driver)
   // state of the last colouring
   int last_cuda = 0;
   cudaStream_t last_stream = nullptr;
@@ -51,7 +53,7 @@ int effective_chunk(const ipgc_options& o) {
 int ctx_device(const ipgc_ctx* ctx) { return ctx->device; }
 int ctx_num_sms(const ipgc_ctx* ctx) { return ctx->num_sms; }
 void ctx_note_cuda_error(ipgc_ctx* ctx, int err) { ctx->last_cuda = err; }
-const float* ctx_policy_weights(const ipgc_ctx* ctx) { return ctx->d_mlp; }
+const float* ctx_policy_weights(const ipgc_ctx* ctx) { return ctx->mlp_len ? ctx->d_mlp : nullptr; }
 
 }  // namespace ipgc
 
@@ -181,8 +183,9 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.policy = o.mode;
   p.max_rounds = o.max_rounds > 0 ? o.max_rounds : (n < INT32_MAX ? n + 1 : INT32_MAX);
   p.timeout_ns = o.timeout_ns ? o.timeout_ns : 10000000000ull;
-  p.mlp = (o.mode == IPGC_MODE_LEARNED) ? ctx->d_mlp : nullptr;
+  p.mlp = (o.mode == IPGC_MODE_LEARNED && ctx->mlp_len) ? ctx->d_mlp : nullptr;
   p.bar_extra = o.fault_inject ? 1u : 0u;
+  p.mlp_margin = o.policy_margin;
   p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
 }
 
@@ -239,6 +242,15 @@ int run_hostloop(ipgc_ctx* ctx, const Params& p, int bs, int blocks, cudaStream_
       mode = IPGC_MODE_DATA;
     else
       mode = total > p.H ? IPGC_MODE_TOPO : IPGC_MODE_DATA;
+    if (p.policy == IPGC_MODE_LEARNED && p.mlp && !ctx->h_mlp.empty()) {
+      // same network and inputs as the device decision, evaluated on the host
+      const Ctrl& c = *ctx->h_ctrl;
+      float f[ipgc::kMlpIn];
+      ipgc::policy_features(p.n, p.nnz, r, total, c.cnt[par][ipgc::B_SMALL], (int64_t)c.dsum[par],
+                            c.maxc, f);
+      const float pr = 1.0f / (1.0f + std::exp(-ipgc::mlp_logit_host(ctx->h_mlp.data(), f)));
+      if (std::fabs(pr - 0.5f) >= p.mlp_margin) mode = pr > 0.5f ? IPGC_MODE_TOPO : IPGC_MODE_DATA;
+    }
     IPGC_CUDA(ctx, ipgc::launch_assign(p, bs, blocks, r, mode, s));
     IPGC_CUDA(ctx, ipgc::launch_detect(p, bs, blocks, r, mode, s));
   }
@@ -259,6 +271,7 @@ void ipgc_options_default(ipgc_options* o) {
   o->max_rounds = 0;
   o->timeout_ns = 0;
   o->validate = 1;
+  o->policy_margin = 0.05f;
 }
 
 const char* ipgc_strerror(int s) {
@@ -338,6 +351,24 @@ int ipgc_ctx_destroy(ipgc_ctx* ctx) {
 }
 
 int ipgc_ctx_cuda_error(const ipgc_ctx* ctx) { return ctx ? ctx->last_cuda : 0; }
+
+int ipgc_policy_load(ipgc_ctx* ctx, const float* w, int32_t len) {
+  if (!ctx) return IPGC_ERR_INVALID;
+  if (len == 0) {
+    ctx->mlp_len = 0;
+    ctx->h_mlp.clear();
+    return IPGC_OK;  // the device copy stays allocated but unused
+  }
+  if (len != ipgc::kMlpParams || !w) return IPGC_ERR_INVALID;
+  for (int32_t i = 0; i < len; ++i)
+    if (!std::isfinite(w[i])) return IPGC_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  if (!ctx->d_mlp) IPGC_CUDA(ctx, cudaMalloc((void**)&ctx->d_mlp, sizeof(float) * ipgc::kMlpParams));
+  IPGC_CUDA(ctx, cudaMemcpy(ctx->d_mlp, w, sizeof(float) * len, cudaMemcpyHostToDevice));
+  ctx->h_mlp.assign(w, w + len);
+  ctx->mlp_len = len;
+  return IPGC_OK;
+}
 
 int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
                   int32_t* colors_out, ipgc_stats* stats_out, const ipgc_options* opt,

@@ -286,6 +286,7 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     p.max_rounds = o.base.max_rounds > 0 ? o.base.max_rounds : (int32_t)n + 1;
     p.timeout_ns = o.base.timeout_ns ? o.base.timeout_ns : 10000000000ull;
     p.mlp = o.base.mode == IPGC_MODE_LEARNED ? d_mlp : nullptr;
+    p.mlp_margin = o.base.policy_margin;
     p.col_vec = ((uintptr_t)p.col & 15u) == 0 ? 1 : 0;
   }
 

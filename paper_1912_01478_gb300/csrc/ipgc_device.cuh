@@ -74,7 +74,71 @@ struct Params {
   const float* mlp;   // learned policy weights (device) or nullptr
   uint32_t bar_extra; // tests only: phantom CTAs every grid barrier waits for
   int32_t col_vec;    // col is 16-byte aligned: int4 loads and bulk L2 prefetches allowed
+  float mlp_margin;   // learned policy: threshold rule when |p - 0.5| < margin
 };
+
+// ------------------------------------------------------- learned policy --
+
+constexpr int kMlpIn = IPGC_MLP_INPUTS;
+constexpr int kMlpH = IPGC_MLP_HIDDEN;
+constexpr int kMlpParams = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;
+static_assert(kMlpParams == IPGC_MLP_PARAMS, "parameter count");
+// offsets of W1[16][8], b1, W2[16][16], b2, w3, b3
+constexpr int kW1 = 0, kB1 = kW1 + kMlpH * kMlpIn, kW2 = kB1 + kMlpH, kB2 = kW2 + kMlpH * kMlpH,
+              kW3 = kB2 + kMlpH, kB3 = kW3 + kMlpH;
+
+// The 8 inputs of the mode decision for a round with worklist size wl (of
+// which wl_small low-degree nodes) and worklist degree sum deg_sum; all of
+// them are known at the start of the round and none depends on the mode.
+__host__ __device__ inline void policy_features(int64_t n, int64_t nnz, int round, int64_t wl,
+                                                int64_t wl_small, int64_t deg_sum, int maxc,
+                                                float f[kMlpIn]) {
+  const float fn = (float)(n > 0 ? n : 1), fe = (float)(nnz > 0 ? nnz : 1);
+  const float fwl = (float)(wl > 0 ? wl : 1);
+  f[0] = (float)wl / fn;
+  f[1] = (float)deg_sum / fe;
+  f[2] = (float)wl_small / fwl;
+  f[3] = log2f(fn + 1.0f) / 32.0f;
+  f[4] = log2f((float)nnz / fn + 1.0f) / 8.0f;
+  f[5] = log2f((float)(round > 0 ? round : 1)) / 16.0f;
+  f[6] = log2f((float)deg_sum / fwl + 1.0f) / 16.0f;
+  f[7] = (float)maxc / ((float)maxc + 64.0f);
+}
+
+// Network logit for inputs f, by one warp (all 32 lanes call; lanes j and
+// j + 16 compute hidden unit j); every lane returns the same value, summed
+// in a fixed order.
+__device__ __forceinline__ float mlp_logit_warp(const float* __restrict__ w, const float f[kMlpIn]) {
+  const int j = threadIdx.x & 15;
+  float a = w[kB1 + j];
+#pragma unroll
+  for (int k = 0; k < kMlpIn; ++k) a += w[kW1 + j * kMlpIn + k] * f[k];
+  const float h1 = tanhf(a);
+  float a2 = w[kB2 + j];
+#pragma unroll
+  for (int k = 0; k < kMlpH; ++k) a2 += w[kW2 + j * kMlpH + k] * __shfl_sync(FULL, h1, k);
+  const float h2 = tanhf(a2);
+  float z = (threadIdx.x & 31) < 16 ? w[kW3 + j] * h2 : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(FULL, z, o);
+  return z + w[kB3];
+}
+
+// The same on the host (host-loop driver).
+inline float mlp_logit_host(const float* w, const float f[kMlpIn]) {
+  float h1[kMlpH], z = w[kB3];
+  for (int j = 0; j < kMlpH; ++j) {
+    float a = w[kB1 + j];
+    for (int k = 0; k < kMlpIn; ++k) a += w[kW1 + j * kMlpIn + k] * f[k];
+    h1[j] = tanhf(a);
+  }
+  for (int j = 0; j < kMlpH; ++j) {
+    float a = w[kB2 + j];
+    for (int k = 0; k < kMlpH; ++k) a += w[kW2 + j * kMlpH + k] * h1[k];
+    z += w[kW3 + j] * tanhf(a);
+  }
+  return z;
+}
 
 __device__ __forceinline__ uint64_t gtime() {
   uint64_t t;

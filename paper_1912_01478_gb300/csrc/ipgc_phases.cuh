@@ -26,6 +26,7 @@ struct Smem {
   int4 stage_t[W][kStageItems];     // staged pushes: static work items (round 1)
   unsigned long long red64[W];
   int red[W];
+  int mode_b;  // broadcast of the round's mode (learned policy)
   unsigned red2[W];
 };
 
@@ -591,6 +592,7 @@ struct RoundView {
   int icnt;    // their work items
   int nistat;  // work items of every high-degree node
   int maxc;    // largest committed colour at round start
+  unsigned long long dsum;  // degree sum of the worklist
 };
 
 __device__ __forceinline__ RoundView read_round(const Params& p, int r) {
@@ -602,6 +604,7 @@ __device__ __forceinline__ RoundView read_round(const Params& p, int r) {
   rv.icnt = ld_cg(&p.ctrl->icnt[rv.par]);
   rv.nistat = ld_cg(&p.ctrl->nistat);
   rv.maxc = ld_cg(&p.ctrl->maxc);
+  rv.dsum = __ldcg(&p.ctrl->dsum[rv.par]);
   rv.mode = MODE_DATA;
   return rv;
 }
@@ -610,6 +613,29 @@ __device__ __forceinline__ int decide_mode(const Params& p, int64_t total) {
   if (p.policy == IPGC_MODE_TOPO) return MODE_TOPO;
   if (p.policy == IPGC_MODE_DATA) return MODE_DATA;
   return total > p.H ? MODE_TOPO : MODE_DATA;
+}
+
+// Mode of the round for every thread of the CTA. With IPGC_MODE_LEARNED and
+// a loaded network, warp 0 evaluates it (every CTA of the team computes the
+// same value from the same inputs); the threshold rule decides when the
+// network is unsure (|p - 0.5| < margin) or absent.
+template <int BS>
+__device__ __forceinline__ int decide_mode_block(const Params& p, const RoundView& rv,
+                                                 int64_t total, Smem<BS>& sm) {
+  if (p.policy != IPGC_MODE_LEARNED || !p.mlp) return decide_mode(p, total);
+  if (threadIdx.x < 32) {
+    float f[kMlpIn];
+    policy_features(p.n, p.nnz, rv.round, total, rv.nsmall, (int64_t)rv.dsum, rv.maxc, f);
+    const float z = mlp_logit_warp(p.mlp, f);
+    if (threadIdx.x == 0) {
+      const float pr = 1.0f / (1.0f + expf(-z));
+      int mode = total > p.H ? MODE_TOPO : MODE_DATA;
+      if (fabsf(pr - 0.5f) >= p.mlp_margin) mode = pr > 0.5f ? MODE_TOPO : MODE_DATA;
+      sm.mode_b = mode;
+    }
+  }
+  __syncthreads();
+  return sm.mode_b;
 }
 
 // Bookkeeping by CTA 0 at the start of round r (after the previous barrier):
@@ -639,6 +665,8 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
     tr.deg_sum = (int64_t)ds;
     tr.max_color = rv.maxc;
     tr.shortcut = 0;
+    tr.wl_small = rv.nsmall;
+    tr.reserved = 0;
     tr.t_begin = gtime();
   }
   __threadfence();
@@ -724,6 +752,8 @@ __device__ __forceinline__ void trace_round1(const Params& p, uint64_t t0) {
     tr.deg_sum = p.nnz;
     tr.max_color = 0;
     tr.shortcut = 1;
+    tr.wl_small = 0;
+    tr.reserved = 0;
     tr.t_begin = t0;
     tr.t_assign = t0;
     tr.t_detect = t1;
@@ -757,7 +787,7 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
         if (lead) atomicCAS(&c->status, 0, IPGC_ERR_NO_CONVERGE);
         break;
       }
-      rv.mode = decide_mode(p, total);
+      rv.mode = decide_mode_block<BS>(p, rv, total, sm);
       round_begin(p, rv, r, total, tm);
       assign_phase<BS>(p, sm, rv, tm);
       if (!team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) break;

@@ -62,6 +62,8 @@ class TraceRec(ctypes.Structure):
         ("deg_sum", ctypes.c_int64),
         ("max_color", ctypes.c_int32),
         ("shortcut", ctypes.c_int32),
+        ("wl_small", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("t_begin", ctypes.c_uint64),
         ("t_assign", ctypes.c_uint64),
         ("t_detect", ctypes.c_uint64),
@@ -76,6 +78,8 @@ TRACE_DTYPE = np.dtype(
         ("deg_sum", np.int64),
         ("max_color", np.int32),
         ("shortcut", np.int32),
+        ("wl_small", np.int32),
+        ("reserved", np.int32),
         ("t_begin", np.uint64),
         ("t_assign", np.uint64),
         ("t_detect", np.uint64),
@@ -100,6 +104,8 @@ class Options(ctypes.Structure):
         ("fin_round", ctypes.c_void_p),
         ("trace_cap", ctypes.c_int32),
         ("fault_inject", ctypes.c_int32),
+        ("policy_margin", ctypes.c_float),
+        ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -170,6 +176,7 @@ class ColorOptions:
     block_size: int = 0
     blocks_per_sm: int = 0
     fault_inject: int = 0
+    policy_margin: float = 0.05
 
     def to_c(self, trace_ptr: int = 0, trace_cap: int = 0, fin_ptr: int = 0) -> Options:
         o = Options()
@@ -186,6 +193,7 @@ class ColorOptions:
         o.trace_cap = trace_cap
         o.fin_round = fin_ptr or None
         o.fault_inject = self.fault_inject
+        o.policy_margin = self.policy_margin
         return o
 
 

@@ -71,9 +71,36 @@ def test_strerror_and_defaults(lib):
     lib.ipgc_options_default(ctypes.byref(o))
     assert o.mode == ipgc.MODE_THRESHOLD and abs(o.threshold_frac - 0.6) < 1e-7
     assert o.driver == ipgc.DRIVER_PERSISTENT and o.validate == 1
-    assert ctypes.sizeof(ipgc.Options) == 72
-    assert ctypes.sizeof(ipgc.Stats) == 40
-    assert ctypes.sizeof(ipgc.TraceRec) == 56
+    assert abs(o.policy_margin - 0.05) < 1e-7
+
+
+def test_ctypes_layouts_match_the_header(tmp_path):
+    # a C program compiled against include/ipgc.h prints the real sizes and
+    # field offsets; the ctypes mirrors must agree field by field
+    from paper_1912_01478_gb300 import batched
+
+    structs = {
+        "ipgc_options": ipgc.Options,
+        "ipgc_stats": ipgc.Stats,
+        "ipgc_trace_rec": ipgc.TraceRec,
+        "ipgc_batch_options": batched.BatchOptions,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ipgc.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
 
 
 def test_workspace_size(lib):

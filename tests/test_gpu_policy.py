@@ -1,0 +1,167 @@
+"""Learned mode switch on the GPU: features, forward pass and gradients of
+the device kernels against the float64 MLP oracle; the Adam step; colours
+unchanged under the learned policy; what the trained network gains over the
+threshold rule on held-out graphs."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1912_01478_gb300 import graphgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1912_01478_gb300 import _build, ipgc
+
+    _build.build()
+    return ipgc.Context(0)
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_features_from_trace(ctx):
+    from paper_1912_01478_gb300 import ipgc, policy
+
+    rp, cl = graphgen.rmat(14, 16, seed=3)
+    import torch
+
+    tr = ipgc.trace_buffer(rp.size + 1)
+    _, st = ctx.color(torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda(), trace=tr)
+    rec = ipgc.read_trace(tr, st.rounds)
+    f = policy.features(tr, st.rounds, rp.size - 1, cl.size).cpu().numpy()
+    n, nnz = rp.size - 1, cl.size
+    wl = np.maximum(rec["wl_size"], 1).astype(np.float64)
+    expect = np.stack([
+        rec["wl_size"] / n,
+        rec["deg_sum"] / nnz,
+        rec["wl_small"] / wl,
+        np.full(st.rounds, np.log2(n + 1.0) / 32),
+        np.full(st.rounds, np.log2(nnz / n + 1.0) / 8),
+        np.log2(np.maximum(rec["round"], 1)) / 16,
+        np.log2(rec["deg_sum"] / wl + 1.0) / 16,
+        rec["max_color"] / (rec["max_color"] + 64.0),
+    ], axis=1)
+    assert np.allclose(f, expect, rtol=1e-5, atol=1e-6)
+    # the low-degree count matches the worklist (round >= 2)
+    deg = np.diff(rp)
+    ref = oracle.color(rp, cl)
+    for r in range(2, st.rounds + 1):
+        active = ref.fin_round >= r
+        assert rec["wl_small"][r - 1] == int(np.sum(active & (deg <= 24)))
+
+
+def test_forward_and_gradient_match_oracle(ctx):
+    from paper_1912_01478_gb300 import policy
+
+    rng = np.random.default_rng(11)
+    for n in (1, 37, 1000, 5000):
+        w = rng.normal(0, 0.5, mlp.NPARAMS).astype(np.float32)
+        x = rng.uniform(0, 1, (n, mlp.IN)).astype(np.float32)
+        y = (rng.uniform(size=n) < 0.4).astype(np.float32)
+        wt = rng.uniform(0.0, 3.0, n).astype(np.float32)
+        wt[0] = max(wt[0], 0.5)
+        p = policy.forward(dev(w), dev(x)).cpu().numpy()
+        assert np.allclose(p, mlp.prob(w.astype(np.float64), x.astype(np.float64)), atol=2e-6)
+        g, loss = policy.grad(dev(w), dev(x), dev(y), dev(wt))
+        g = g.cpu().numpy().astype(np.float64)
+        g_ref = mlp.grad(w.astype(np.float64), x.astype(np.float64), y, wt.astype(np.float64))
+        assert abs(loss - mlp.loss(w.astype(np.float64), x, y, wt)) < 1e-5
+        scale = np.max(np.abs(g_ref))
+        assert np.max(np.abs(g - g_ref)) <= 1e-4 * scale + 1e-7, n
+
+
+def test_adam_step_and_training(ctx):
+    from paper_1912_01478_gb300 import policy
+
+    rng = np.random.default_rng(12)
+    n = 2000
+    x = rng.uniform(0, 1, (n, mlp.IN)).astype(np.float32)
+    y = (x[:, 0] + 0.3 * x[:, 1] > 0.7).astype(np.float32)
+    wt = np.ones(n, np.float32)
+    w0 = policy.init_weights(seed=3)
+    # one step: Adam's first update is lr * g / (|g| + eps) in every coordinate
+    w1, _ = policy.train(ctx, dev(x), dev(y), dev(wt), epochs=1, lr=0.01, w0=w0.copy())
+    g_ref = mlp.grad(w0.astype(np.float64), x, y, wt)
+    expect, _, _ = mlp.adam_step(w0.astype(np.float64), 0.0, 0.0, g_ref, 1, lr=0.01)
+    big = np.abs(g_ref) > 1e-5
+    assert np.allclose(w1[big], expect[big], atol=2e-6)
+    # training separates a learnable rule: loss falls well below log 2
+    w, loss = policy.train(ctx, dev(x), dev(y), dev(wt), epochs=800, lr=0.02, seed=4)
+    assert loss < 0.25
+    acc = np.mean((mlp.prob(w.astype(np.float64), x) > 0.5) == (y > 0.5))
+    assert acc > 0.95
+    # deterministic: the same run again gives the same weights bit for bit
+    w_again, _ = policy.train(ctx, dev(x), dev(y), dev(wt), epochs=800, lr=0.02, seed=4)
+    assert np.array_equal(w, w_again)
+
+
+TRAIN = [("rmat", 15, 16, 1), ("rmat", 16, 8, 2), ("rmat", 17, 16, 3), ("road", 512, 0, 4),
+         ("road", 1024, 0, 5), ("er", 200_000, 8, 6), ("er", 60_000, 32, 7), ("rmat", 18, 8, 8)]
+HELD = [("rmat", 16, 16, 21), ("rmat", 17, 8, 22), ("road", 768, 0, 23), ("er", 120_000, 16, 24)]
+
+
+def make(kind, a, b, seed):
+    if kind == "rmat":
+        return graphgen.rmat(a, b, seed=seed)
+    if kind == "road":
+        return graphgen.road(a, seed=seed)
+    return graphgen.er(a, a * b // 2, seed=seed)
+
+
+@pytest.mark.slow
+def test_learned_policy_gain_and_parity(ctx):
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc, policy
+
+    train_tr = policy.collect(ctx, [make(*g) for g in TRAIN])
+    held_graphs = [make(*g) for g in HELD]
+    held_tr = policy.collect(ctx, held_graphs)
+    w, loss = policy.train(ctx, dev(train_tr.x), dev(train_tr.y),
+                           dev(train_tr.w / max(train_tr.w.mean(), 1e-9)), epochs=1500, lr=0.01)
+    choice, p = policy.decisions(w, held_tr.x, 0.05, held_tr.thr_topo)
+    t_thr = held_tr.totals(held_tr.thr_topo)
+    t_learned = held_tr.totals(choice)
+    t_best = float(np.minimum(held_tr.t_topo, held_tr.t_data).sum())
+    t_data = held_tr.totals(np.zeros_like(choice))
+    gain = t_thr / t_learned
+    print(f"\nheld-out round time: threshold {t_thr/1e6:.3f} ms, learned {t_learned/1e6:.3f} ms "
+          f"(gain {gain:.3f}x), all-data {t_data/1e6:.3f} ms, per-round best {t_best/1e6:.3f} ms")
+    # the trained network does not lose to the rule it falls back on
+    assert t_learned <= t_thr * 1.02
+    # colours under the learned policy are the oracle's, in both drivers
+    policy.load(ctx, w)
+    for rp, cl in held_graphs[:2]:
+        ref = oracle.color(rp, cl, trace=False)
+        drp, dcl = torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda()
+        for driver in ("persistent", "hostloop"):
+            colors, st = ctx.color(drp, dcl, options=ipgc.ColorOptions(mode="learned", driver=driver))
+            assert np.array_equal(colors.cpu().numpy(), ref.colors) and st.rounds == ref.rounds
+    policy.load(ctx, None)
+
+
+def test_learned_without_network_is_threshold(ctx):
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc, policy
+
+    policy.load(ctx, None)
+    rp, cl = graphgen.road(300, seed=9)
+    drp, dcl = torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda()
+    _, a = ctx.color(drp, dcl, options=ipgc.ColorOptions(mode="learned"))
+    _, b = ctx.color(drp, dcl, options=ipgc.ColorOptions(mode="threshold"))
+    assert (a.rounds_topo, a.rounds_data) == (b.rounds_topo, b.rounds_data)
+    # a network that always says "topology" switches every round after the first
+    w = np.zeros(433, np.float32)
+    w[432] = 10.0
+    policy.load(ctx, w)
+    _, c = ctx.color(drp, dcl, options=ipgc.ColorOptions(mode="learned"))
+    assert c.rounds_data == 0 and c.rounds_topo == c.rounds
+    policy.load(ctx, None)
