@@ -243,6 +243,67 @@ IPGC_API int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t
                                 void* stream);
 
 /*
+ * Colouring server with continuous batching. Requests are host
+ * CSR graphs, copied into pinned staging at submission and queued in order.
+ * A scheduler thread admits queued requests while the device arena (one
+ * allocation of hbm_budget bytes) has room for the graph, its colours and its
+ * working set, copies them to the device, and colours every admitted request
+ * in one batched launch whenever one of `inflight` batch slots is free; the
+ * slots run concurrently on their own streams, so requests arriving while
+ * others are on the GPU start without waiting for them to finish, and a
+ * completed batch's memory admits the next requests at once. Each result is
+ * the colouring the graph gets alone (the batched phases). The learned mode
+ * policy is not used by the server (IPGC_MODE_LEARNED runs the threshold rule).
+ */
+typedef struct ipgc_server ipgc_server;
+
+typedef struct ipgc_server_options {
+  size_t hbm_budget;          /* device arena bytes; default 8 GiB */
+  size_t host_budget;         /* pinned staging bytes; default 4 GiB */
+  int32_t inflight;           /* concurrent batches, 1..8; default 2 */
+  int32_t max_batch_graphs;   /* graphs per launch; default 1024 */
+  int32_t max_pending;        /* queued, not yet admitted requests; default 65536 */
+  int32_t reserved;
+  ipgc_batch_options batch;   /* schedule and mode (base.validate: check each CSR on submit) */
+} ipgc_server_options;
+
+typedef struct ipgc_server_counters {
+  uint64_t submitted, completed, batches, graphs_in_batches;
+  int64_t pending;            /* queued, waiting for device memory */
+  int64_t ready;              /* admitted, waiting for a batch slot */
+  int32_t running_batches;
+  int32_t max_batch;          /* largest batch launched so far */
+  int64_t hbm_used, hbm_peak; /* device arena bytes in use / at most */
+  int64_t host_used;          /* pinned staging bytes in use */
+  int32_t status;             /* IPGC_OK or the error that stopped the server */
+  int32_t reserved;
+} ipgc_server_counters;
+
+IPGC_API void ipgc_server_options_default(ipgc_server_options* opt);
+/* Allocates the arenas and starts the scheduler thread on `device`. */
+IPGC_API int ipgc_server_create(ipgc_server** out, int device, const ipgc_server_options* opt);
+/*
+ * Queue one graph (HOST pointers, copied before the call returns).
+ * IPGC_ERR_TOO_LARGE: it can never fit the budgets; IPGC_ERR_BUSY: the
+ * queue or the staging is full right now (retry later); IPGC_ERR_INVALID.
+ */
+IPGC_API int ipgc_server_submit(ipgc_server* srv, const int32_t* h_rowptr, const int32_t* h_col,
+                                int32_t n, int64_t nnz, uint64_t* ticket);
+/*
+ * IPGC_PENDING while the request runs. Otherwise copies its colours to
+ * h_colors (host int32[n], may be NULL), its statistics and its latency
+ * (submission to completion, ns; may be NULL), releases the ticket and
+ * returns its status; IPGC_ERR_NOT_FOUND for an unknown or released ticket.
+ */
+IPGC_API int ipgc_server_poll(ipgc_server* srv, uint64_t ticket, int32_t* h_colors,
+                              ipgc_stats* stats, int64_t* latency_ns);
+/* The next completed ticket (each reported once); IPGC_PENDING after timeout_ns. */
+IPGC_API int ipgc_server_next_done(ipgc_server* srv, uint64_t* ticket, uint64_t timeout_ns);
+IPGC_API int ipgc_server_query(ipgc_server* srv, ipgc_server_counters* counters);
+/* Finishes admitted work, drops queued requests, frees everything. */
+IPGC_API int ipgc_server_destroy(ipgc_server* srv);
+
+/*
  * Learned mode switch. A multilayer perceptron 8 -> 16 -> 16 -> 1 (tanh
  * hidden units, logistic output) gives the probability that the round runs
  * faster topology-driven than data-driven (Section IV leaves the choice of H

@@ -60,13 +60,88 @@ cudaError_t occupancy_batched(int bs, int* blocks_per_sm) {
   });
 }
 
-cudaError_t launch_batched(const BatchParams& bp, int bs, int blocks, cudaStream_t s) {
+cudaError_t launch_batched(const BatchParams& bp, int bs, int blocks, bool cooperative,
+                           cudaStream_t s) {
   return with_block(bs, [&](auto B) {
     BatchParams q = bp;
+    if (!cooperative) {
+      batched_kernel<decltype(B)::value><<<blocks, decltype(B)::value, 0, s>>>(q);
+      return cudaGetLastError();
+    }
     void* args[] = {&q};
     return cudaLaunchCooperativeKernel((const void*)batched_kernel<decltype(B)::value>,
                                        dim3(blocks), dim3(decltype(B)::value), args, 0, s);
   });
+}
+
+// Schedule: graphs with at least team_min_nnz entries go to teams of
+// team_size CTAs (largest first onto the least-loaded team, load = n + nnz);
+// the rest to single CTAs through a shared counter, largest first. Copies
+// the parameters and lists to the device and launches on `grid` CTAs.
+// Control blocks must already be zeroed. *rc receives IPGC_ERR_UNSUPPORTED
+// when the lists do not fit lists_cap ints.
+cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int team_size,
+                                int64_t team_min_nnz, bool cooperative, Params* d_params,
+                                int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,
+                                cudaStream_t s, int* rc) {
+  *rc = IPGC_OK;
+  int nteams = grid / team_size;
+  if (nteams < 1) {
+    nteams = 1;
+    team_size = grid;
+  }
+  std::vector<int32_t> order(G);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return h_params[a].nnz > h_params[b].nnz; });
+  std::vector<std::vector<int32_t>> per_team(nteams);
+  std::vector<int32_t> solo;
+  using Load = std::pair<int64_t, int32_t>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int32_t t = 0; t < nteams; ++t) heap.push({0, t});
+  for (int32_t g : order) {
+    const int64_t n = h_params[g].n, e = h_params[g].nnz;
+    if (n == 0) continue;
+    if (e >= team_min_nnz && team_size > 1) {
+      Load l = heap.top();
+      heap.pop();
+      per_team[l.second].push_back(g);
+      heap.push({l.first + e + n, l.second});
+    } else {
+      solo.push_back(g);
+    }
+  }
+  lists.clear();
+  std::vector<int32_t> team_off(nteams + 1, 0);
+  for (int32_t t = 0; t < nteams; ++t) {
+    team_off[t + 1] = team_off[t] + (int32_t)per_team[t].size();
+    lists.insert(lists.end(), per_team[t].begin(), per_team[t].end());
+  }
+  const size_t n_team_list = lists.size();
+  lists.insert(lists.end(), team_off.begin(), team_off.end());
+  lists.insert(lists.end(), solo.begin(), solo.end());
+  lists.push_back(0);  // solo queue counter
+  if (lists.size() > lists_cap) {
+    *rc = IPGC_ERR_UNSUPPORTED;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_params, h_params, sizeof(Params) * (size_t)G,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_lists, lists.data(), sizeof(int32_t) * lists.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  BatchParams bp;
+  bp.params = d_params;
+  bp.team_list = d_lists;
+  bp.team_off = d_lists + n_team_list;
+  bp.solo_list = d_lists + n_team_list + (nteams + 1);
+  bp.nsolo = (int32_t)solo.size();
+  bp.team_size = team_size;
+  bp.nteams = nteams;
+  bp.solo_next = d_lists + n_team_list + (nteams + 1) + solo.size();
+  return launch_batched(bp, bs, nteams * team_size > grid ? nteams * team_size : grid, cooperative,
+                        s);
 }
 
 }  // namespace ipgc
@@ -290,68 +365,15 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     p.col_vec = ((uintptr_t)p.col & 15u) == 0 ? 1 : 0;
   }
 
-  // schedule: large graphs to teams (largest first onto the least-loaded
-  // team), the rest to single CTAs in a shared queue, largest first
   int occ = 0;
   BCUDA(ipgc::occupancy_batched(bs, &occ));
-  const int sms = ipgc::ctx_num_sms(ctx);
-  int team_size = o.team_size;
-  int nteams = occ * sms / team_size;
-  if (nteams < 1) {
-    nteams = 1;
-    team_size = occ * sms;
-  }
-  const int blocks = std::max(nteams * team_size, occ * sms);
-  std::vector<int32_t> order(num_graphs);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return edge_off[a + 1] - edge_off[a] > edge_off[b + 1] - edge_off[b];
-  });
-  std::vector<std::vector<int32_t>> per_team(nteams);
-  std::vector<int32_t> solo;
-  using Load = std::pair<int64_t, int32_t>;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int32_t t = 0; t < nteams; ++t) heap.push({0, t});
-  for (int32_t g : order) {
-    const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
-    if (n == 0) continue;
-    if (e >= o.team_min_nnz && team_size > 1) {
-      Load l = heap.top();
-      heap.pop();
-      per_team[l.second].push_back(g);
-      heap.push({l.first + e + n, l.second});
-    } else {
-      solo.push_back(g);
-    }
-  }
-  W->lists.clear();
-  std::vector<int32_t> team_off(nteams + 1, 0);
-  for (int32_t t = 0; t < nteams; ++t) {
-    team_off[t + 1] = team_off[t] + (int32_t)per_team[t].size();
-    W->lists.insert(W->lists.end(), per_team[t].begin(), per_team[t].end());
-  }
-  const size_t n_team_list = W->lists.size();
-  W->lists.insert(W->lists.end(), team_off.begin(), team_off.end());
-  W->lists.insert(W->lists.end(), solo.begin(), solo.end());
-  W->lists.push_back(0);  // solo queue counter
-  if (W->lists.size() * sizeof(int32_t) > b_lists) return IPGC_ERR_UNSUPPORTED;
-
-  BCUDA(cudaMemcpyAsync(d_params, W->params.data(), sizeof(Params) * (size_t)num_graphs,
-                        cudaMemcpyHostToDevice, s));
-  BCUDA(cudaMemcpyAsync(d_lists, W->lists.data(), sizeof(int32_t) * W->lists.size(),
-                        cudaMemcpyHostToDevice, s));
+  const int grid = occ * ipgc::ctx_num_sms(ctx);
   BCUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl) * (size_t)num_graphs, s));
-
-  BatchParams bp;
-  bp.params = d_params;
-  bp.team_list = d_lists;
-  bp.team_off = d_lists + n_team_list;
-  bp.solo_list = d_lists + n_team_list + (nteams + 1);
-  bp.nsolo = (int32_t)solo.size();
-  bp.team_size = team_size;
-  bp.nteams = nteams;
-  bp.solo_next = d_lists + n_team_list + (nteams + 1) + solo.size();
-  BCUDA(ipgc::launch_batched(bp, bs, blocks, s));
+  int rc = IPGC_OK;
+  BCUDA(ipgc::schedule_and_launch(W->params.data(), num_graphs, bs, grid, o.team_size,
+                                  o.team_min_nnz, true, d_params, d_lists,
+                                  b_lists / sizeof(int32_t), W->lists, s, &rc));
+  if (rc != IPGC_OK) return rc;
 
   if (!per_graph_stats) return IPGC_OK;
   BCUDA(cudaMemcpyAsync(W->h_ctrl, d_ctrl, sizeof(Ctrl) * (size_t)num_graphs,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <type_traits>
+#include <vector>
 
 #include "ipgc_device.cuh"
 
@@ -34,6 +35,10 @@ cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int32_t n
 
 // Batched colouring (ipgc_batched.cu).
 cudaError_t occupancy_batched(int bs, int* blocks_per_sm);
+cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int team_size,
+                                int64_t team_min_nnz, bool cooperative, Params* d_params,
+                                int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,
+                                cudaStream_t s, int* rc);
 
 // Context accessors (ipgc_api.cu).
 int ctx_device(const ipgc_ctx* ctx);

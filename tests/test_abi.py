@@ -77,13 +77,15 @@ def test_strerror_and_defaults(lib):
 def test_ctypes_layouts_match_the_header(tmp_path):
     # a C program compiled against include/ipgc.h prints the real sizes and
     # field offsets; the ctypes mirrors must agree field by field
-    from paper_1912_01478_gb300 import batched
+    from paper_1912_01478_gb300 import batched, server
 
     structs = {
         "ipgc_options": ipgc.Options,
         "ipgc_stats": ipgc.Stats,
         "ipgc_trace_rec": ipgc.TraceRec,
         "ipgc_batch_options": batched.BatchOptions,
+        "ipgc_server_options": server.ServerOptions,
+        "ipgc_server_counters": server.ServerCounters,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ipgc.h"', "int main(void) {"]
     for cname, cls in structs.items():

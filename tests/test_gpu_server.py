@@ -1,0 +1,120 @@
+"""Colouring server: continuous batching gives every request the colouring
+it gets alone (the CPU oracle's), whatever else is in flight; admission by
+device memory, slot reuse, errors."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_01478_gb300 import graphgen
+
+pytestmark = pytest.mark.gpu
+
+
+def pool(k, seed, nmax=60_000):
+    bt = graphgen.batch(k, seed=seed, nmin=100, nmax=nmax)
+    return [tuple(np.ascontiguousarray(a) for a in graphgen.batch_graph(bt, g)) for g in range(k)]
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    gs = pool(40, seed=5)
+    gs.append(graphgen.rmat(16, 16, seed=6))  # one large request (teams)
+    refs = [oracle.color(rp, cl, trace=False) for rp, cl in gs]
+    return gs, refs
+
+
+def check(res, ref):
+    colors, st, lat = res
+    assert np.array_equal(colors, ref.colors)
+    assert st.rounds == ref.rounds and st.num_colors == ref.num_colors and st.error == 0
+    assert lat > 0
+
+
+def test_results_same_alone_and_in_the_mix(graphs):
+    from paper_1912_01478_gb300 import _build, server
+
+    _build.build()
+    gs, refs = graphs
+    srv = server.Server(0, server.options(inflight=2, max_batch_graphs=8))
+    # alone: one request at a time
+    alone = []
+    for rp, cl in gs[:6]:
+        t = srv.submit(rp, cl)
+        while (r := srv.poll(t)) is None:
+            time.sleep(0.0005)
+        alone.append(r)
+    for r, ref in zip(alone, refs[:6]):
+        check(r, ref)
+    # in the mix: everything at once from two submitting threads, results
+    # polled in completion order; small batches force several overlapping ones
+    tickets = [None] * len(gs)
+
+    def submit_range(lo, hi):
+        for i in range(lo, hi):
+            tickets[i] = srv.submit(*gs[i])
+
+    th = [threading.Thread(target=submit_range, args=(0, 20)),
+          threading.Thread(target=submit_range, args=(20, len(gs)))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    got = {}
+    deadline = time.time() + 60
+    while len(got) < len(gs) and time.time() < deadline:
+        t = srv.next_done(timeout_s=1.0)
+        if t is not None:
+            got[t] = srv.poll(t)
+    assert len(got) == len(gs)
+    for i, t in enumerate(tickets):
+        check(got[t], refs[i])
+    c = srv.counters()
+    assert c.batches >= 2 and c.completed == c.submitted and c.hbm_used == 0 and c.status == 0
+    srv.close()
+
+
+def test_admission_by_device_memory(graphs):
+    # a budget that holds only a couple of requests at a time: the rest wait
+    # in the queue and are admitted as memory frees up
+    from paper_1912_01478_gb300 import server
+
+    gs, refs = graphs
+    small = gs[:30]
+    srv = server.Server(0, server.options(hbm_budget=24 << 20, inflight=2, max_batch_graphs=4))
+    tickets = [srv.submit(rp, cl) for rp, cl in small]
+    for t, ref in zip(tickets, refs[:30]):
+        while (r := srv.poll(t)) is None:
+            time.sleep(0.0005)
+        check(r, ref)
+    c = srv.counters()
+    assert c.hbm_peak <= 24 << 20 and c.hbm_used == 0 and c.batches >= 8
+    srv.close()
+
+
+def test_errors_and_ticket_reuse(graphs):
+    from paper_1912_01478_gb300 import ipgc, server
+
+    gs, refs = graphs
+    srv = server.Server(0, server.options(hbm_budget=8 << 20, host_budget=64 << 20))
+    rp, cl = graphgen.rmat(17, 16, seed=1)  # needs more than 8 MB on the device
+    with pytest.raises(ipgc.IpgcError) as ei:
+        srv.submit(rp, cl)
+    assert ei.value.code == ipgc.IPGC_ERR_TOO_LARGE
+    t = srv.submit(*gs[0])
+    while (r := srv.poll(t)) is None:
+        time.sleep(0.0005)
+    check(r, refs[0])
+    with pytest.raises(ipgc.IpgcError) as ei:
+        srv.poll(t)  # released
+    assert ei.value.code == ipgc.IPGC_ERR_NOT_FOUND
+    # an empty graph completes at once
+    t0 = srv.submit(np.zeros(1, np.int32), np.zeros(0, np.int32))
+    r0 = srv.poll(t0)
+    assert r0 is not None and r0[1].rounds == 0
+    # destroy with work queued: no hang, no leak of the context
+    for rp2, cl2 in gs[:10]:
+        srv.submit(rp2, cl2)
+    srv.close()
