@@ -56,7 +56,114 @@ def parse():
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched workload (0 = skip the batched leg)")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000",
+                    help="request rates of the serving leg (empty = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     return ap.parse_args()
+
+
+def serving_leg(args, ctx, dev, stream):
+    """Serving: Poisson request streams at each rate, graphs drawn from a pool
+    shaped like the batched workload (512 graphs) plus RMAT scale-20 graphs
+    (edge factor 16) for 1 % of the requests; seed 5. Requests go to the
+    continuous-batching server by reference from pinned memory; latency =
+    submission to completion. The plain path serves the same stream one
+    request at a time through ipgc_color_host (copies inside each call)."""
+    import torch
+
+    from paper_1912_01478_gb300 import graphgen, server
+
+    rates = [int(r) for r in args.serve_rates.split(",") if r]
+    if not rates:
+        return None
+    bt = graphgen.batch(512, seed=5, nmin=100, nmax=200_000)
+    pool = [graphgen.batch_graph(bt, g) for g in range(512)]
+    big = [graphgen.rmat(20, 16, seed=500 + k) for k in range(4)]
+    pinned = []
+    for rp, cl in pool + big:
+        prp = torch.from_numpy(np.ascontiguousarray(rp)).pin_memory()
+        pcl = torch.from_numpy(np.ascontiguousarray(cl)).pin_memory()
+        pinned.append((prp, pcl, prp.numpy(), pcl.numpy()))
+    del bt
+    rng = np.random.default_rng(5)
+    out_rates = []
+    for rate in rates:
+        N = max(1, int(rate * args.serve_seconds))
+        gaps = rng.exponential(1.0 / rate, N)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        pick = np.where(rng.uniform(size=N) < 0.01, 512 + rng.integers(0, 4, N), rng.integers(0, 512, N))
+        srv = server.Server(dev.index or 0, server.options(
+            hbm_budget=24 << 30, host_budget=2 << 30, inflight=2, max_batch_graphs=1024))
+        lat = []
+        done_n = [0]
+
+        def drain():
+            while done_n[0] < N:
+                t = srv.next_done(timeout_s=5.0)
+                if t is None:
+                    break
+                r = srv.poll(t)
+                lat.append(r[2])
+                done_n[0] += 1
+
+        import threading
+
+        th = threading.Thread(target=drain, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        busy_retries = 0
+        for i in range(N):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            _, _, rp, cl = pinned[pick[i]]
+            while True:
+                try:
+                    srv.submit_ref(rp, cl)
+                    break
+                except Exception as e:  # queue or staging momentarily full
+                    if getattr(e, "code", None) != -6:
+                        raise
+                    busy_retries += 1
+                    time.sleep(0.0001)
+        th.join(timeout=120)
+        wall = time.perf_counter() - t0
+        c = srv.counters()
+        srv.close()
+        lat_ms = np.array(lat, dtype=np.float64) / 1e6
+        # plain path on the first requests of the same stream
+        M = min(N, 200)
+        plain_lat = []
+        tp0 = time.perf_counter()
+        for i in range(M):
+            while time.perf_counter() - tp0 < arrivals[i]:
+                pass
+            _, _, rp, cl = pinned[pick[i]]
+            ctx.color_host(rp, cl, options=None, stream=stream)
+            plain_lat.append(time.perf_counter() - tp0 - arrivals[i])
+        plain_wall = time.perf_counter() - tp0
+        pl = np.array(plain_lat) * 1e3
+        out_rates.append({
+            "rate_rps": rate,
+            "requests": N,
+            "completed": int(len(lat)),
+            "throughput_rps": len(lat) / wall,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
+            "batches": int(c.batches),
+            "mean_batch": c.graphs_in_batches / max(int(c.batches), 1),
+            "hbm_peak_gb": c.hbm_peak / 2**30,
+            "busy_retries": busy_retries,
+            "plain_requests": M,
+            "plain_throughput_rps": M / plain_wall,
+            "plain_p50_ms": float(np.percentile(pl, 50)),
+            "plain_p99_ms": float(np.percentile(pl, 99)),
+        })
+    return {
+        "workload": "Poisson arrivals per rate; graphs drawn from 512 graphs shaped like the batched "
+                    "workload (seed 5) and, for 1 % of requests, 4 RMAT scale-20 edge-factor-16 graphs",
+        "seconds_per_rate": args.serve_seconds,
+        "rates": out_rates,
+    }
 
 
 def batched_leg(args, ctx, dev, stream):
@@ -229,7 +336,7 @@ class ClockSampler:
 
 
 def algorithmic_bytes(rp, cl, fin, modes):
-    """Bytes the method must move, summed over rounds (see DESIGN.md):
+    """Bytes the method must move, summed over rounds:
     round 1 (implicit assignment): rowptr, the first neighbour of every
     non-isolated node, colour and tentative-colour writes, loser pushes;
     round r >= 2 over the active set A (D = sum deg, L = sum of lower-ID
@@ -404,6 +511,10 @@ def main():
         del drp, dcl, colors
         torch.cuda.empty_cache()
         batched_out = batched_leg(args, ctx, dev, stream)
+    serving_out = None
+    if world == 1 and args.serve_rates:
+        torch.cuda.empty_cache()
+        serving_out = serving_leg(args, ctx, dev, stream)
     hbm, src = peaks()
     avg_launch_s = float(np.mean(per_launch_ms)) / 1e3
     achieved_gbs = alg_bytes / avg_launch_s / 1e9
@@ -455,6 +566,7 @@ def main():
         "clocks": clk.summary(),
         "cpu_baseline": ({k: v for k, v in cpu.items() if k != "seconds"} if cpu else None),
         "batched": batched_out,
+        "serving": serving_out,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

@@ -204,16 +204,19 @@ IPGC_API int ipgc_validate_csr(ipgc_ctx* ctx, const int32_t* rowptr, const int32
 /*
  * Batched colouring: many independent graphs in one persistent launch. Each
  * graph gets exactly the colouring ipgc_color_ex would give it alone (own
- * worklists, rounds and mode decisions, Sections II-C and IV); graphs with at
- * least team_min_nnz entries are coloured by teams of team_size CTAs, the
- * others by one CTA each. Options in `base` apply to every graph (trace,
- * fin_round, driver, blocks_per_sm and fault_inject are ignored).
+ * worklists, rounds and mode decisions, Sections II-C and IV). A graph is
+ * coloured by a team of k CTAs, k the smallest power of two with
+ * k * nnz_per_cta >= its entries, or min(max_team, grid) where that is
+ * smaller; teams are gang-scheduled on aligned blocks of CTAs, largest
+ * first, and graphs with k = 1 are taken one CTA each from a shared queue. Options in `base` apply
+ * to every graph (trace, fin_round, driver, blocks_per_sm and fault_inject
+ * are ignored).
  */
 typedef struct ipgc_batch_options {
   ipgc_options base;     /* defaults as ipgc_options_default, but validate = 0 */
-  int32_t team_size;     /* CTAs per team for large graphs (1..64); default 8 */
+  int32_t max_team;      /* largest team in CTAs, >= 0 (0: the whole grid); default 0 */
   int32_t reserved;
-  int64_t team_min_nnz;  /* entries from which a graph goes to a team; default 262144 */
+  int64_t nnz_per_cta;   /* entries per CTA of a team, >= 1; default 131072 */
 } ipgc_batch_options;
 
 IPGC_API void ipgc_batch_options_default(ipgc_batch_options* opt);
@@ -243,16 +246,33 @@ IPGC_API int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t
                                 void* stream);
 
 /*
- * Colouring server with continuous batching (SURVEY S1). Requests are host
+ * The schedule ipgc_color_batched uses on `grid` CTAs, computed on the host
+ * (no device needed). Inputs: n[g], nnz[g] per graph (HOST arrays). Outputs
+ * (HOST int32[num_graphs], caller-owned): team[g] = CTAs colouring graph g
+ * (0: empty graph, 1: the single-CTA queue); first_cta[g] = first CTA of its
+ * aligned block of team[g] CTAs (-1 for team[g] <= 1); seq[g] = position in
+ * the gang order of the teams (every CTA runs its team jobs in this order)
+ * or in the single-CTA queue (-1 for empty graphs). IPGC_OK or
+ * IPGC_ERR_INVALID.
+ */
+IPGC_API int ipgc_batch_plan(int32_t num_graphs, const int32_t* n, const int64_t* nnz,
+                             int32_t grid, int32_t max_team, int64_t nnz_per_cta, int32_t* team,
+                             int32_t* first_cta, int32_t* seq);
+
+/*
+ * Colouring server with continuous batching. Requests are host
  * CSR graphs, copied into pinned staging at submission and queued in order.
  * A scheduler thread admits queued requests while the device arena (one
  * allocation of hbm_budget bytes) has room for the graph, its colours and its
  * working set, copies them to the device, and colours every admitted request
  * in one batched launch whenever one of `inflight` batch slots is free; the
  * slots run concurrently on their own streams, so requests arriving while
- * others are on the GPU start without waiting for them to finish, and a
- * completed batch's memory admits the next requests at once. Each result is
- * the colouring the graph gets alone (the batched phases). The learned mode
+ * others are on the GPU start without waiting for them to finish. Each
+ * request completes as soon as its own graph is coloured (the kernel writes
+ * the result into pinned staging and raises a host-visible flag), not when
+ * its batch ends, and its device memory then admits the next requests at
+ * once. Each result is the colouring the graph gets alone (the batched
+ * phases). The learned mode
  * policy is not used by the server (IPGC_MODE_LEARNED runs the threshold rule).
  */
 typedef struct ipgc_server ipgc_server;
@@ -289,6 +309,15 @@ IPGC_API int ipgc_server_create(ipgc_server** out, int device, const ipgc_server
  */
 IPGC_API int ipgc_server_submit(ipgc_server* srv, const int32_t* h_rowptr, const int32_t* h_col,
                                 int32_t n, int64_t nnz, uint64_t* ticket);
+/*
+ * The same without the copy: the server reads the graph from the caller's
+ * arrays when it admits the request, so they must stay valid and unchanged
+ * until the ticket completes. Page-locked (pinned) arrays let the copy to the
+ * device run asynchronously; pageable ones are copied synchronously.
+ */
+IPGC_API int ipgc_server_submit_ref(ipgc_server* srv, const int32_t* h_rowptr,
+                                    const int32_t* h_col, int32_t n, int64_t nnz,
+                                    uint64_t* ticket);
 /*
  * IPGC_PENDING while the request runs. Otherwise copies its colours to
  * h_colors (host int32[n], may be NULL), its statistics and its latency
@@ -344,8 +373,8 @@ IPGC_API int ipgc_mlp_train(ipgc_ctx* ctx, const float* x, const float* y, const
 IPGC_API int ipgc_policy_load(ipgc_ctx* ctx, const float* w, int32_t len);
 
 /*
- * Schedule autotuners (SURVEY B2). The schedule (t1, chunk, block_size and,
- * for batches, team_size and team_min_nnz) changes speed only, never a
+ * Schedule autotuners. The schedule (t1, chunk, block_size and,
+ * for batches, max_team and nnz_per_cta) changes speed only, never a
  * colour. Starting from *opt, each knob in turn is set to every candidate
  * value, the colouring is timed (best of `reps`, CUDA events on `stream`) and
  * the fastest value is kept; *opt receives the result and *best_ms (may be

@@ -11,9 +11,9 @@ from . import ipgc
 class BatchOptions(ctypes.Structure):
     _fields_ = [
         ("base", ipgc.Options),
-        ("team_size", ctypes.c_int32),
+        ("max_team", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
-        ("team_min_nnz", ctypes.c_int64),
+        ("nnz_per_cta", ctypes.c_int64),
     ]
 
 
@@ -24,6 +24,10 @@ SIGNATURES = {
         ctypes.c_int,
         [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.POINTER(ipgc.Stats),
          ctypes.POINTER(BatchOptions), _P],
+    ),
+    "ipgc_batch_plan": (
+        ctypes.c_int,
+        [ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P, _P],
     ),
     "ipgc_batched_autotune": (
         ctypes.c_int,
@@ -50,9 +54,26 @@ def autotune(ctx: "ipgc.Context", node_off, edge_off, rowptr_cat, col_cat, color
     return o, best.value
 
 
+def plan(n, nnz, grid: int, max_team: int = 0, nnz_per_cta: int = 131072):
+    """The gang schedule of a batch on `grid` CTAs (host only): per graph its
+    team size, the first CTA of its block (-1: single CTA or empty) and its
+    position in the gang order or the single-CTA queue (-1: empty)."""
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    nnz = np.ascontiguousarray(nnz, dtype=np.int64)
+    G = n.size
+    team = np.zeros(G, np.int32)
+    first = np.zeros(G, np.int32)
+    seq = np.zeros(G, np.int32)
+    rc = lib().ipgc_batch_plan(G, n.ctypes.data, nnz.ctypes.data, grid, max_team, nnz_per_cta,
+                               team.ctypes.data, first.ctypes.data, seq.ctypes.data)
+    if rc != ipgc.IPGC_OK:
+        raise ipgc.IpgcError(rc, "ipgc_batch_plan")
+    return team, first, seq
+
+
 def describe(o: BatchOptions) -> dict:
     return dict(t1=o.base.t1, chunk=o.base.chunk, block_size=o.base.block_size,
-                team_size=o.team_size, team_min_nnz=int(o.team_min_nnz), mode=o.base.mode)
+                max_team=o.max_team, nnz_per_cta=int(o.nnz_per_cta), mode=o.base.mode)
 
 _bound = False
 
@@ -69,17 +90,19 @@ def lib():
     return L
 
 
-def options(team_size: int = 0, team_min_nnz: int = -1, **base) -> BatchOptions:
-    """Batch options: defaults, then team settings and ipgc.ColorOptions fields."""
+def options(max_team: int = -1, nnz_per_cta: int = 0, **base) -> BatchOptions:
+    """Batch options: defaults, then team settings (max_team: largest team in
+    CTAs, 0 = the grid; nnz_per_cta: entries per team CTA) and
+    ipgc.ColorOptions fields."""
     o = BatchOptions()
     lib().ipgc_batch_options_default(ctypes.byref(o))
     if base:
         b = ipgc.ColorOptions(**{"validate": False, **base}).to_c()
         o.base = b
-    if team_size:
-        o.team_size = team_size
-    if team_min_nnz >= 0:
-        o.team_min_nnz = team_min_nnz
+    if max_team >= 0:
+        o.max_team = max_team
+    if nnz_per_cta:
+        o.nnz_per_cta = nnz_per_cta
     return o
 
 

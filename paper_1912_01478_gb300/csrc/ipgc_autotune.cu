@@ -127,9 +127,9 @@ int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node
   std::vector<Knob<ipgc_batch_options>> knobs = {
       {[](ipgc_batch_options& o, int64_t v) { o.base.chunk = (int32_t)v; }, {512, 1024, 2048}},
       {[](ipgc_batch_options& o, int64_t v) { o.base.t1 = (int32_t)v; }, {16, 24, 40, 63}},
-      {[](ipgc_batch_options& o, int64_t v) { o.team_min_nnz = v; },
-       {1 << 16, 1 << 18, 1 << 20, (int64_t)1 << 40}},
-      {[](ipgc_batch_options& o, int64_t v) { o.team_size = (int32_t)v; }, {2, 4, 8, 16}},
+      {[](ipgc_batch_options& o, int64_t v) { o.nnz_per_cta = v; },
+       {1 << 14, 1 << 16, 1 << 17, 1 << 18, 1 << 20, (int64_t)1 << 40}},
+      {[](ipgc_batch_options& o, int64_t v) { o.max_team = (int32_t)v; }, {0, 4, 16, 64}},
       {[](ipgc_batch_options& o, int64_t v) { o.base.block_size = (int32_t)v; }, {256, 512}},
   };
   const int rc = descend(

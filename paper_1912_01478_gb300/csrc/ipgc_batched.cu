@@ -4,11 +4,12 @@
 // Every graph runs its own round loop (its own worklists, round counter, mode
 // decision and control block) with exactly the single-graph phases of
 // ipgc_phases.cuh, so each graph's colours equal those of colouring it alone.
-// Large graphs are coloured by teams of `team_size` CTAs that separate their
-// rounds with a bounded team barrier; the host deals them to the teams
-// largest-first onto the least-loaded team. Every other graph is coloured by
-// a single CTA that takes graphs, largest first, from a shared counter once
-// its team's list is done, so the short graphs fill the tail.
+// A graph with many entries is coloured by a team of CTAs (a power of two in
+// size, growing with the graph) that separate its rounds with a bounded team
+// barrier; the host gang-schedules the teams onto aligned blocks of CTAs.
+// Every other graph is coloured by a single CTA that takes graphs, largest
+// first, from a shared counter once its own team jobs are done, so the short
+// graphs fill the tail.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -24,24 +25,25 @@ namespace ipgc {
 
 struct BatchParams {
   const Params* params;       // [G] per-graph parameters
-  const int32_t* team_list;   // graphs of team t: team_list[team_off[t] .. team_off[t + 1])
-  const int32_t* team_off;    // [nteams + 1]
+  const int4* jobs;           // {graph, rank in its team, team size, 0}
+  const int32_t* cta_off;     // CTA c runs jobs[cta_off[c] .. cta_off[c + 1]) in order
   const int32_t* solo_list;   // graphs coloured by one CTA each, largest first
   int32_t nsolo;
-  int32_t team_size;
-  int32_t nteams;
   int32_t* solo_next;         // shared counter over solo_list (zeroed before launch)
 };
 
+// Every CTA first runs its own list of team jobs. The lists are cut from one
+// global job order, so the team of the earliest unfinished job can always
+// meet at its barriers and no two teams wait on each other in a cycle. Then
+// every CTA takes single-CTA graphs from the shared counter.
 template <int BS>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) batched_kernel(BatchParams bp) {
   __shared__ Smem<BS> sm;
   __shared__ int s_k;
   smem_clear<BS>(sm);
-  const int team = blockIdx.x / bp.team_size, rank = blockIdx.x % bp.team_size;
-  if (team < bp.nteams) {
-    for (int i = bp.team_off[team]; i < bp.team_off[team + 1]; ++i)
-      color_graph<BS>(bp.params[bp.team_list[i]], sm, Team{rank, bp.team_size});
+  for (int j = bp.cta_off[blockIdx.x]; j < bp.cta_off[blockIdx.x + 1]; ++j) {
+    const int4 jb = bp.jobs[j];
+    color_graph<BS>(bp.params[jb.x], sm, Team{jb.y, jb.z});
   }
   for (;;) {
     __syncthreads();
@@ -74,57 +76,92 @@ cudaError_t launch_batched(const BatchParams& bp, int bs, int blocks, bool coope
   });
 }
 
-// Schedule: graphs with at least team_min_nnz entries go to teams of
-// team_size CTAs (largest first onto the least-loaded team, load = n + nnz);
-// the rest to single CTAs through a shared counter, largest first. Copies
-// the parameters and lists to the device and launches on `grid` CTAs.
-// Control blocks must already be zeroed. *rc receives IPGC_ERR_UNSUPPORTED
-// when the lists do not fit lists_cap ints.
-cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int team_size,
-                                int64_t team_min_nnz, bool cooperative, Params* d_params,
-                                int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,
-                                cudaStream_t s, int* rc) {
-  *rc = IPGC_OK;
-  int nteams = grid / team_size;
-  if (nteams < 1) {
-    nteams = 1;
-    team_size = grid;
-  }
+// Schedule of a batch on `grid` CTAs. A graph's team size k is the smallest
+// power of two with k * nnz_per_cta >= nnz, or cap = min(max_team (0: the
+// grid), grid) when that power is larger (cap itself need not be a power of
+// two, so the largest graphs can use every CTA). Graphs with k = 1 go to the
+// shared single-CTA queue, largest first. The others are gang-scheduled
+// largest team first, then largest work first: each takes the block of k
+// consecutive CTAs starting at a multiple of k whose busiest CTA is least
+// loaded, and every CTA of the block is then busy until that load plus the
+// graph's work / k (work = n + nnz). Since larger teams come first and all
+// smaller sizes are powers of two, every candidate block is evenly loaded
+// when a team is placed, so no CTA idles waiting for its team. Jobs are
+// appended to the CTAs' lists in this one global order. Lists layout
+// (int32): jobs as int4 (16-byte aligned first), cta_off[grid + 1], solo
+// list, queue counter.
+void build_schedule(const Params* h_params, int32_t G, int grid, int max_team,
+                    int64_t nnz_per_cta, std::vector<int32_t>& lists, int32_t* njobs_out,
+                    int32_t* nsolo_out, int32_t* seq_out) {
+  const int cap = max_team > 0 && max_team < grid ? max_team : grid;
   std::vector<int32_t> order(G);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int32_t a, int32_t b) { return h_params[a].nnz > h_params[b].nnz; });
-  std::vector<std::vector<int32_t>> per_team(nteams);
+  std::vector<int32_t> team(G, 0);
+  for (int32_t g = 0; g < G; ++g) {
+    if (h_params[g].n == 0) continue;
+    const int64_t need = nnz_per_cta > 0 ? (h_params[g].nnz + nnz_per_cta - 1) / nnz_per_cta : 1;
+    int64_t k = 1;
+    while (k < need && k < cap) k *= 2;
+    team[g] = (int32_t)std::min<int64_t>(k, cap);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    if (team[a] != team[b]) return team[a] > team[b];
+    return h_params[a].nnz + h_params[a].n > h_params[b].nnz + h_params[b].n;
+  });
+  std::vector<double> load(grid, 0.0);
+  std::vector<std::vector<int4>> per_cta(grid);
   std::vector<int32_t> solo;
-  using Load = std::pair<int64_t, int32_t>;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int32_t t = 0; t < nteams; ++t) heap.push({0, t});
+  int32_t njobs = 0, nteam = 0;
   for (int32_t g : order) {
-    const int64_t n = h_params[g].n, e = h_params[g].nnz;
-    if (n == 0) continue;
-    if (e >= team_min_nnz && team_size > 1) {
-      Load l = heap.top();
-      heap.pop();
-      per_team[l.second].push_back(g);
-      heap.push({l.first + e + n, l.second});
-    } else {
+    const int k = team[g];
+    if (seq_out) seq_out[g] = -1;
+    if (k == 0) continue;
+    if (k == 1) {
+      if (seq_out) seq_out[g] = (int32_t)solo.size();
       solo.push_back(g);
+      continue;
     }
+    if (seq_out) seq_out[g] = nteam;
+    ++nteam;
+    int best = 0;
+    double best_start = 1e300;
+    for (int b = 0; b + k <= grid; b += k) {
+      double m = 0;
+      for (int c = b; c < b + k; ++c) m = std::max(m, load[c]);
+      if (m < best_start) {
+        best_start = m;
+        best = b;
+      }
+    }
+    const double finish = best_start + (double)(h_params[g].nnz + h_params[g].n) / k;
+    for (int c = best; c < best + k; ++c) {
+      load[c] = finish;
+      per_cta[c].push_back(make_int4(g, c - best, k, 0));
+    }
+    njobs += k;
   }
   lists.clear();
-  std::vector<int32_t> team_off(nteams + 1, 0);
-  for (int32_t t = 0; t < nteams; ++t) {
-    team_off[t + 1] = team_off[t] + (int32_t)per_team[t].size();
-    lists.insert(lists.end(), per_team[t].begin(), per_team[t].end());
+  lists.reserve(4 * (size_t)njobs + grid + 1 + solo.size() + 1);
+  std::vector<int32_t> cta_off(grid + 1, 0);
+  for (int c = 0; c < grid; ++c) {
+    cta_off[c + 1] = cta_off[c] + (int32_t)per_cta[c].size();
+    for (const int4& j : per_cta[c]) {
+      lists.push_back(j.x);
+      lists.push_back(j.y);
+      lists.push_back(j.z);
+      lists.push_back(j.w);
+    }
   }
-  const size_t n_team_list = lists.size();
-  lists.insert(lists.end(), team_off.begin(), team_off.end());
+  lists.insert(lists.end(), cta_off.begin(), cta_off.end());
   lists.insert(lists.end(), solo.begin(), solo.end());
   lists.push_back(0);  // solo queue counter
-  if (lists.size() > lists_cap) {
-    *rc = IPGC_ERR_UNSUPPORTED;
-    return cudaSuccess;
-  }
+  *njobs_out = njobs;
+  *nsolo_out = (int32_t)solo.size();
+}
+
+cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid, bool cooperative,
+                            const std::vector<int32_t>& lists, int32_t njobs, int32_t nsolo,
+                            Params* d_params, int32_t* d_lists, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(d_params, h_params, sizeof(Params) * (size_t)G,
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -133,15 +170,27 @@ cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int g
   if (e != cudaSuccess) return e;
   BatchParams bp;
   bp.params = d_params;
-  bp.team_list = d_lists;
-  bp.team_off = d_lists + n_team_list;
-  bp.solo_list = d_lists + n_team_list + (nteams + 1);
-  bp.nsolo = (int32_t)solo.size();
-  bp.team_size = team_size;
-  bp.nteams = nteams;
-  bp.solo_next = d_lists + n_team_list + (nteams + 1) + solo.size();
-  return launch_batched(bp, bs, nteams * team_size > grid ? nteams * team_size : grid, cooperative,
-                        s);
+  bp.jobs = reinterpret_cast<const int4*>(d_lists);
+  bp.cta_off = d_lists + 4 * (size_t)njobs;
+  bp.solo_list = bp.cta_off + grid + 1;
+  bp.nsolo = nsolo;
+  bp.solo_next = d_lists + 4 * (size_t)njobs + grid + 1 + nsolo;
+  return launch_batched(bp, bs, grid, cooperative, s);
+}
+
+cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int max_team,
+                                int64_t nnz_per_cta, bool cooperative, Params* d_params,
+                                int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,
+                                cudaStream_t s, int* rc) {
+  *rc = IPGC_OK;
+  int32_t njobs = 0, nsolo = 0;
+  build_schedule(h_params, G, grid, max_team, nnz_per_cta, lists, &njobs, &nsolo, nullptr);
+  if (lists.size() > lists_cap) {
+    *rc = IPGC_ERR_UNSUPPORTED;
+    return cudaSuccess;
+  }
+  return launch_schedule(h_params, G, bs, grid, cooperative, lists, njobs, nsolo, d_params,
+                         d_lists, s);
 }
 
 }  // namespace ipgc
@@ -205,8 +254,8 @@ void ipgc_batch_options_default(ipgc_batch_options* o) {
   std::memset(o, 0, sizeof(*o));
   ipgc_options_default(&o->base);
   o->base.validate = 0;
-  o->team_size = 8;
-  o->team_min_nnz = 262144;
+  o->max_team = 0;
+  o->nnz_per_cta = 131072;
 }
 
 int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_off,
@@ -219,7 +268,7 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     o = *opt;
   else
     ipgc_batch_options_default(&o);
-  if (o.team_size < 1 || o.team_size > 64) return IPGC_ERR_INVALID;
+  if (o.max_team < 0 || o.nnz_per_cta < 1) return IPGC_ERR_INVALID;
   if (o.base.mode < IPGC_MODE_THRESHOLD || o.base.mode > IPGC_MODE_LEARNED) return IPGC_ERR_INVALID;
   if (o.base.block_size != 0 && o.base.block_size != 256 && o.base.block_size != 512)
     return IPGC_ERR_UNSUPPORTED;
@@ -262,8 +311,20 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     item_base[g + 1] = item_base[g] + e / chunk + nbig + 1;
     gbase[g + 1] = gbase[g] + e / ((int64_t)chunk + 1) + 1;
   }
+  // the schedule needs only the shapes, so it is built first and sizes its buffer
+  W->params.assign(num_graphs, Params());
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    W->params[g].n = (int32_t)(node_off[g + 1] - node_off[g]);
+    W->params[g].nnz = edge_off[g + 1] - edge_off[g];
+  }
+  int occ = 0;
+  BCUDA(ipgc::occupancy_batched(bs, &occ));
+  const int grid = occ * ipgc::ctx_num_sms(ctx);
+  int32_t njobs = 0, nsolo = 0;
+  ipgc::build_schedule(W->params.data(), num_graphs, grid, o.max_team, o.nnz_per_cta, W->lists,
+                       &njobs, &nsolo, nullptr);
   const size_t b_params = al256(sizeof(Params) * (size_t)num_graphs);
-  const size_t b_lists = al256(sizeof(int32_t) * ((size_t)2 * num_graphs + 64 * 1024 + 16));
+  const size_t b_lists = al256(sizeof(int32_t) * W->lists.size());
   const size_t b_ctrl = al256(sizeof(Ctrl) * (size_t)num_graphs);
   const size_t b_node = al256(sizeof(int32_t) * (size_t)total_n);
   const size_t b_items = al256(sizeof(int4) * (size_t)item_base[num_graphs]);
@@ -331,7 +392,6 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   }
 
   // per-graph parameters
-  W->params.resize(num_graphs);
   const float* d_mlp = ipgc::ctx_policy_weights(ctx);
   for (int32_t g = 0; g < num_graphs; ++g) {
     Params& p = W->params[g];
@@ -365,15 +425,9 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     p.col_vec = ((uintptr_t)p.col & 15u) == 0 ? 1 : 0;
   }
 
-  int occ = 0;
-  BCUDA(ipgc::occupancy_batched(bs, &occ));
-  const int grid = occ * ipgc::ctx_num_sms(ctx);
   BCUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl) * (size_t)num_graphs, s));
-  int rc = IPGC_OK;
-  BCUDA(ipgc::schedule_and_launch(W->params.data(), num_graphs, bs, grid, o.team_size,
-                                  o.team_min_nnz, true, d_params, d_lists,
-                                  b_lists / sizeof(int32_t), W->lists, s, &rc));
-  if (rc != IPGC_OK) return rc;
+  BCUDA(ipgc::launch_schedule(W->params.data(), num_graphs, bs, grid, true, W->lists, njobs, nsolo,
+                              d_params, d_lists, s));
 
   if (!per_graph_stats) return IPGC_OK;
   BCUDA(cudaMemcpyAsync(W->h_ctrl, d_ctrl, sizeof(Ctrl) * (size_t)num_graphs,
@@ -395,6 +449,35 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     if (c.status != IPGC_OK && worst == IPGC_OK) worst = c.status;
   }
   return worst;
+}
+
+int ipgc_batch_plan(int32_t num_graphs, const int32_t* n, const int64_t* nnz, int32_t grid,
+                    int32_t max_team, int64_t nnz_per_cta, int32_t* team, int32_t* first_cta,
+                    int32_t* seq) {
+  if (num_graphs < 0 || grid < 1 || max_team < 0 || nnz_per_cta < 1) return IPGC_ERR_INVALID;
+  if (num_graphs > 0 && (!n || !nnz || !team || !first_cta || !seq)) return IPGC_ERR_INVALID;
+  std::vector<Params> ps(num_graphs, Params());
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    if (n[g] < 0 || nnz[g] < 0) return IPGC_ERR_INVALID;
+    ps[g].n = n[g];
+    ps[g].nnz = nnz[g];
+  }
+  std::vector<int32_t> lists;
+  int32_t njobs = 0, nsolo = 0;
+  ipgc::build_schedule(ps.data(), num_graphs, grid, max_team, nnz_per_cta, lists, &njobs, &nsolo,
+                       seq);
+  for (int32_t g = 0; g < num_graphs; ++g) {
+    team[g] = seq[g] < 0 ? 0 : 1;
+    first_cta[g] = -1;
+  }
+  const int32_t* cta_off = lists.data() + 4 * (size_t)njobs;
+  for (int32_t c = 0; c < grid; ++c)
+    for (int32_t j = cta_off[c]; j < cta_off[c + 1]; ++j) {
+      const int32_t* jb = lists.data() + 4 * (size_t)j;
+      team[jb[0]] = jb[2];
+      first_cta[jb[0]] = c - jb[1];
+    }
+  return IPGC_OK;
 }
 
 }  // extern "C"

@@ -42,7 +42,8 @@ struct Ctrl {
   unsigned long long edges;        // sum over rounds of the worklist degree sums
   unsigned long long t_start, t_end;
   unsigned long long t_prev_assign, t_prev_detect;  // previous round's phase times
-  int32_t pad[8];
+  int32_t ctas_done;               // team CTAs that have published their share of the result
+  int32_t pad[7];
 };
 
 struct Params {
@@ -75,6 +76,13 @@ struct Params {
   uint32_t bar_extra; // tests only: phantom CTAs every grid barrier waits for
   int32_t col_vec;    // col is 16-byte aligned: int4 loads and bulk L2 prefetches allowed
   float mlp_margin;   // learned policy: threshold rule when |p - 0.5| < margin
+  // Optional result publication into host-mapped pinned memory (nullptr:
+  // none). When a graph is done its team copies the colours to out_colors
+  // and the control block to out_ctrl, then sets *out_done = 1, so the host
+  // sees each graph complete while the rest of its launch still runs.
+  int32_t* out_colors;
+  Ctrl* out_ctrl;
+  int32_t* out_done;
 };
 
 // ------------------------------------------------------- learned policy --

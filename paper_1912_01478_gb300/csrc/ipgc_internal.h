@@ -35,10 +35,24 @@ cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int32_t n
 
 // Batched colouring (ipgc_batched.cu).
 cudaError_t occupancy_batched(int bs, int* blocks_per_sm);
-cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int team_size,
-                                int64_t team_min_nnz, bool cooperative, Params* d_params,
+// Schedule of a batch on `grid` CTAs (int32 lists, see build_schedule), then
+// its upload and launch; lists_cap bounds the device list buffer (rc =
+// IPGC_ERR_UNSUPPORTED when the schedule does not fit).
+void build_schedule(const Params* h_params, int32_t G, int grid, int max_team,
+                    int64_t nnz_per_cta, std::vector<int32_t>& lists, int32_t* njobs_out,
+                    int32_t* nsolo_out, int32_t* seq_out);
+cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid, bool cooperative,
+                            const std::vector<int32_t>& lists, int32_t njobs, int32_t nsolo,
+                            Params* d_params, int32_t* d_lists, cudaStream_t s);
+cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int max_team,
+                                int64_t nnz_per_cta, bool cooperative, Params* d_params,
                                 int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,
                                 cudaStream_t s, int* rc);
+// Upper bound on the list length build_schedule makes for G graphs with
+// teams of at most kmax CTAs each on `grid` CTAs.
+inline size_t schedule_lists_bound(int32_t G, int grid, int kmax) {
+  return 4 * (size_t)G * (size_t)kmax + (size_t)grid + 1 + (size_t)G + 1;
+}
 
 // Context accessors (ipgc_api.cu).
 int ctx_device(const ipgc_ctx* ctx);

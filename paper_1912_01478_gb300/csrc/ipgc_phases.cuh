@@ -763,6 +763,43 @@ __device__ __forceinline__ void trace_round1(const Params& p, uint64_t t0) {
 
 // ----------------------------------------------------------- one colouring --
 
+// Result publication into host-mapped memory. Every CTA of the team copies
+// its slice of the final colours (read from L2: other CTAs wrote them) and
+// fences at system scope before it counts itself done; the CTA that counts
+// last copies the control block and then raises the host flag, so a host that
+// sees the flag sees the whole result.
+template <int BS>
+__device__ void publish_result(const Params& p, Team tm) {
+  const int64_t n = p.n;
+  int64_t lo = n * tm.cta / tm.ncta, hi = n * (tm.cta + 1) / tm.ncta;
+  const bool vec = (((uintptr_t)p.color | (uintptr_t)p.out_colors) & 15u) == 0;
+  if (vec) {
+    // slices rounded to multiples of 4 nodes: int4 copies, scalar tail
+    lo &= ~int64_t(3);
+    hi = tm.cta + 1 == tm.ncta ? n : (hi & ~int64_t(3));
+    const int64_t v_hi = lo + ((hi - lo) & ~int64_t(3));
+    const int4* src = reinterpret_cast<const int4*>(p.color);
+    int4* dst = reinterpret_cast<int4*>(p.out_colors);
+    for (int64_t i = lo / 4 + threadIdx.x; i < v_hi / 4; i += BS) dst[i] = ld_cg4(src + i);
+    for (int64_t i = v_hi + threadIdx.x; i < hi; i += BS) p.out_colors[i] = ld_cg(p.color + i);
+  } else {
+    for (int64_t i = lo + threadIdx.x; i < hi; i += BS) p.out_colors[i] = ld_cg(p.color + i);
+  }
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int prev = atomicAdd(&p.ctrl->ctas_done, 1);
+    if (prev == tm.ncta - 1) {
+      __threadfence();
+      const volatile uint32_t* s = reinterpret_cast<const volatile uint32_t*>(p.ctrl);
+      volatile uint32_t* d = reinterpret_cast<volatile uint32_t*>(p.out_ctrl);
+      for (int i = 0; i < (int)(sizeof(Ctrl) / 4); ++i) d[i] = s[i];
+      __threadfence_system();
+      *reinterpret_cast<volatile int32_t*>(p.out_done) = 1;
+    }
+  }
+}
+
 // The whole round loop of one graph by a team of CTAs (the whole grid for the
 // single-graph kernel, a few CTAs or one CTA for a graph of a batch), the
 // rounds separated by the team's bounded barrier.
@@ -802,6 +839,7 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
     }
   }
   if (lead) c->t_end = gtime();
+  if (p.out_done) publish_result<BS>(p, tm);
 }
 
 }  // namespace ipgc

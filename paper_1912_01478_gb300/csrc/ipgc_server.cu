@@ -8,9 +8,12 @@
 // in one batched launch on that slot's stream (the phases of a single-graph
 // colouring, so every result is the one the graph gets alone); slots run
 // concurrently, and requests admitted while batches are running start in the
-// next free slot. When a batch completes, its colours are already on the
-// way back to staging; the requests' device memory returns to the arena at
-// once, so waiting requests are admitted as memory frees up.
+// next free slot. Each request completes on its own: the team that colours it
+// writes the colours and the control block straight into pinned staging
+// through its device mapping and then raises the request's flag, which the
+// scheduler polls, so a small request does not wait for a large one in the
+// same launch; its device memory returns to the arena at once, so waiting
+// requests are admitted as memory frees up.
 //
 // Batches run as ordinary launches of at most 1/inflight of the device's
 // resident CTAs each, so all CTAs of every in-flight batch fit on the GPU at
@@ -94,7 +97,10 @@ enum class St { Pending, Ready, Running, Done, Failed };
 struct Request {
   int32_t n = 0;
   int64_t nnz = 0;
-  size_t h_off = 0, h_bytes = 0;  // staging: rowptr, col, colours
+  size_t h_off = 0, h_bytes = 0;  // staging: rowptr, col, colours (colours only by reference)
+  size_t h_colors = 0;            // offset of the colours inside the staging block
+  const int32_t* ref_rowptr = nullptr;  // caller's arrays (submission by reference)
+  const int32_t* ref_col = nullptr;
   size_t d_off = 0, d_bytes = 0;  // device: rowptr, col, colours, working set
   St st = St::Pending;
   Clock::time_point t_submit, t_done;
@@ -110,10 +116,16 @@ struct Slot {
   int32_t* d_lists = nullptr;
   size_t lists_cap = 0;
   Ctrl* d_ctrl = nullptr;
-  Ctrl* h_ctrl = nullptr;  // pinned
+  // pinned, written by the kernel through their device mappings: each
+  // graph's control block and its completion flag
+  Ctrl* h_ctrl = nullptr;
+  int32_t* h_done = nullptr;
+  Ctrl* m_ctrl = nullptr;
+  int32_t* m_done = nullptr;
   std::vector<Params> params;
   std::vector<int32_t> lists;
   std::vector<uint64_t> tickets;
+  std::vector<char> finished;  // ticket i already completed from its flag
 };
 
 // Per-request device layout (offsets from the request's block).
@@ -160,9 +172,10 @@ size_t host_bytes(int32_t n, int64_t nnz) {
 struct ipgc_server {
   int device = 0;
   ipgc_server_options opt{};
-  int t1 = 0, chunk = 0, bs = 256, grid = 0, team_size = 8;
+  int t1 = 0, chunk = 0, bs = 256, grid = 0, max_team = 1;
   char* d_arena = nullptr;
   char* h_arena = nullptr;  // pinned
+  char* m_arena = nullptr;  // h_arena's device mapping
   Arena dev, host;
   cudaStream_t copy_stream = nullptr;
   std::vector<Slot> slots;
@@ -195,34 +208,49 @@ void fail_all_locked(ipgc_server* S, int err) {
   S->cv_done.notify_all();
 }
 
-// Completes finished batches; returns true when something changed.
+// One request's result is in staging: statistics from its control block,
+// its device memory back to the arena (no CTA touches it any more).
+void complete_locked(ipgc_server* S, uint64_t ticket, const Ctrl& c, int err) {
+  Request& r = S->reqs[ticket];
+  r.stats.rounds = c.rounds;
+  r.stats.num_colors = c.maxc;
+  r.stats.rounds_topo = c.rounds_topo;
+  r.stats.rounds_data = c.rounds_data;
+  r.stats.edges_processed = (int64_t)c.edges;
+  r.stats.ns = c.t_end >= c.t_start ? c.t_end - c.t_start : 0;
+  r.stats.error = err != IPGC_OK ? err : c.status;
+  r.err = r.stats.error;
+  r.st = r.err == IPGC_OK ? St::Done : St::Failed;
+  r.t_done = Clock::now();
+  S->dev.release(r.d_off, r.d_bytes);
+  S->done_q.push_back(ticket);
+  ++S->n_completed;
+}
+
+// Completes every graph whose flag is up, and frees the slots of finished
+// launches; returns true when something changed.
 bool reap_locked(ipgc_server* S) {
   bool any = false;
   for (Slot& sl : S->slots) {
     if (!sl.busy) continue;
+    for (size_t i = 0; i < sl.tickets.size(); ++i) {
+      if (sl.finished[i] || __atomic_load_n(sl.h_done + i, __ATOMIC_ACQUIRE) == 0) continue;
+      complete_locked(S, sl.tickets[i], sl.h_ctrl[i], IPGC_OK);
+      sl.finished[i] = 1;
+      any = true;
+    }
     const cudaError_t q = cudaEventQuery(sl.done);
     if (q == cudaErrorNotReady) continue;
     sl.busy = false;
     any = true;
-    const Clock::time_point now = Clock::now();
+    // a finished launch has raised every flag; anything else is a failure
     for (size_t i = 0; i < sl.tickets.size(); ++i) {
-      Request& r = S->reqs[sl.tickets[i]];
-      const Ctrl& c = sl.h_ctrl[i];
-      r.stats.rounds = c.rounds;
-      r.stats.num_colors = c.maxc;
-      r.stats.rounds_topo = c.rounds_topo;
-      r.stats.rounds_data = c.rounds_data;
-      r.stats.edges_processed = (int64_t)c.edges;
-      r.stats.ns = c.t_end >= c.t_start ? c.t_end - c.t_start : 0;
-      r.stats.error = q == cudaSuccess ? c.status : IPGC_ERR_CUDA;
-      r.err = r.stats.error;
-      r.st = r.err == IPGC_OK ? St::Done : St::Failed;
-      r.t_done = now;
-      S->dev.release(r.d_off, r.d_bytes);
-      S->done_q.push_back(sl.tickets[i]);
-      ++S->n_completed;
+      if (sl.finished[i]) continue;
+      const bool up = q == cudaSuccess && __atomic_load_n(sl.h_done + i, __ATOMIC_ACQUIRE) != 0;
+      complete_locked(S, sl.tickets[i], sl.h_ctrl[i], up ? IPGC_OK : IPGC_ERR_CUDA);
     }
     sl.tickets.clear();
+    sl.finished.clear();
     if (q != cudaSuccess) {
       fail_all_locked(S, IPGC_ERR_CUDA);
       return true;
@@ -243,11 +271,14 @@ bool admit_locked(ipgc_server* S) {
     const DevLayout L = dev_layout(r.n, r.nnz, S->t1, S->chunk);
     char* dbase = S->d_arena + off;
     const char* hbase = S->h_arena + r.h_off;
-    cudaError_t e = cudaMemcpyAsync(dbase + L.rowptr, hbase, 4 * ((size_t)r.n + 1),
+    const void* src_rp = r.ref_rowptr ? (const void*)r.ref_rowptr : (const void*)hbase;
+    const void* src_col = r.ref_rowptr ? (const void*)r.ref_col
+                                       : (const void*)(hbase + al256(4 * ((size_t)r.n + 1)));
+    cudaError_t e = cudaMemcpyAsync(dbase + L.rowptr, src_rp, 4 * ((size_t)r.n + 1),
                                     cudaMemcpyHostToDevice, S->copy_stream);
     if (e == cudaSuccess && r.nnz > 0)
-      e = cudaMemcpyAsync(dbase + L.col, hbase + al256(4 * ((size_t)r.n + 1)), 4 * (size_t)r.nnz,
-                          cudaMemcpyHostToDevice, S->copy_stream);
+      e = cudaMemcpyAsync(dbase + L.col, src_col, 4 * (size_t)r.nnz, cudaMemcpyHostToDevice,
+                          S->copy_stream);
     if (e != cudaSuccess) {
       fail_all_locked(S, IPGC_ERR_CUDA);
       return true;
@@ -277,8 +308,10 @@ bool launch_locked(ipgc_server* S) {
   }
   const int32_t G = (int32_t)std::min<size_t>(S->ready.size(), (size_t)S->opt.max_batch_graphs);
   sl->tickets.assign(S->ready.begin(), S->ready.begin() + G);
+  sl->finished.assign(G, 0);
   S->ready.erase(S->ready.begin(), S->ready.begin() + G);
   sl->params.resize(G);
+  std::memset(sl->h_done, 0, sizeof(int32_t) * (size_t)G);  // the slot's last launch is over
   for (int32_t i = 0; i < G; ++i) {
     Request& r = S->reqs[sl->tickets[i]];
     r.st = St::Running;
@@ -311,27 +344,19 @@ bool launch_locked(ipgc_server* S) {
     p.max_rounds = r.n + 1;
     p.timeout_ns = S->opt.batch.base.timeout_ns ? S->opt.batch.base.timeout_ns : 10000000000ull;
     p.col_vec = 1;  // arena blocks are 256-byte aligned
+    // the team publishes the result straight into staging (256-byte aligned)
+    p.out_colors = (int32_t*)(S->m_arena + r.h_off + r.h_colors);
+    p.out_ctrl = sl->m_ctrl + i;
+    p.out_done = sl->m_done + i;
   }
   int rc = IPGC_OK;
   cudaError_t e = cudaEventRecord(copied, S->copy_stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(sl->stream, copied, 0);
   if (e == cudaSuccess) e = cudaMemsetAsync(sl->d_ctrl, 0, sizeof(Ctrl) * (size_t)G, sl->stream);
   if (e == cudaSuccess)
-    e = ipgc::schedule_and_launch(sl->params.data(), G, S->bs, S->grid, S->team_size,
-                                  S->opt.batch.team_min_nnz, false, sl->d_params, sl->d_lists,
+    e = ipgc::schedule_and_launch(sl->params.data(), G, S->bs, S->grid, S->max_team,
+                                  S->opt.batch.nnz_per_cta, false, sl->d_params, sl->d_lists,
                                   sl->lists_cap, sl->lists, sl->stream, &rc);
-  for (int32_t i = 0; e == cudaSuccess && i < G; ++i) {
-    const Request& r = S->reqs[sl->tickets[i]];
-    if (r.n == 0) continue;
-    const DevLayout L = dev_layout(r.n, r.nnz, S->t1, S->chunk);
-    char* hcol = S->h_arena + r.h_off + al256(4 * ((size_t)r.n + 1)) +
-                 al256(4 * (size_t)(r.nnz > 0 ? r.nnz : 1));
-    e = cudaMemcpyAsync(hcol, S->d_arena + r.d_off + L.colors, 4 * (size_t)r.n,
-                        cudaMemcpyDeviceToHost, sl->stream);
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl->h_ctrl, sl->d_ctrl, sizeof(Ctrl) * (size_t)G, cudaMemcpyDeviceToHost,
-                        sl->stream);
   if (e == cudaSuccess) e = cudaEventRecord(sl->done, sl->stream);
   cudaEventDestroy(copied);
   if (e != cudaSuccess || rc != IPGC_OK) {
@@ -375,6 +400,7 @@ void destroy_resources(ipgc_server* S) {
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.d_params) cudaFree(s.d_params);
     if (s.h_ctrl) cudaFreeHost(s.h_ctrl);
+    if (s.h_done) cudaFreeHost(s.h_done);
   }
   if (S->copy_stream) {
     cudaStreamSynchronize(S->copy_stream);
@@ -408,7 +434,8 @@ int ipgc_server_create(ipgc_server** out, int device, const ipgc_server_options*
   else
     ipgc_server_options_default(&o);
   if (o.inflight < 1 || o.inflight > 8 || o.max_batch_graphs < 1 || o.max_pending < 1 ||
-      o.hbm_budget < 4096 || o.host_budget < 4096 || o.batch.team_size < 1)
+      o.hbm_budget < 4096 || o.host_budget < 4096 || o.batch.max_team < 0 ||
+      o.batch.nnz_per_cta < 1)
     return IPGC_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return IPGC_ERR_INVALID;
@@ -426,24 +453,31 @@ int ipgc_server_create(ipgc_server** out, int device, const ipgc_server_options*
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     rc = IPGC_ERR_CUDA;
   S->grid = occ * sms / o.inflight;
-  S->team_size = std::min(o.batch.team_size, std::max(1, S->grid));
+  // largest team: max_team (0: the grid), at most the grid
+  S->max_team = o.batch.max_team > 0 && o.batch.max_team < S->grid ? o.batch.max_team : S->grid;
+  if (S->max_team < 1) S->max_team = 1;
   if (rc == IPGC_OK && S->grid < 1) rc = IPGC_ERR_UNSUPPORTED;
   if (rc == IPGC_OK && cudaMalloc((void**)&S->d_arena, o.hbm_budget) != cudaSuccess) rc = IPGC_ERR_OOM;
   if (rc == IPGC_OK && cudaMallocHost((void**)&S->h_arena, o.host_budget) != cudaSuccess)
     rc = IPGC_ERR_OOM;
+  if (rc == IPGC_OK && cudaHostGetDevicePointer((void**)&S->m_arena, S->h_arena, 0) != cudaSuccess)
+    rc = IPGC_ERR_CUDA;
   if (rc == IPGC_OK &&
       cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
     rc = IPGC_ERR_CUDA;
   S->slots.resize(o.inflight);
   for (Slot& s : S->slots) {
     if (rc != IPGC_OK) break;
-    s.lists_cap = 2 * (size_t)o.max_batch_graphs + (size_t)S->grid + 16;
+    s.lists_cap = ipgc::schedule_lists_bound(o.max_batch_graphs, S->grid, S->max_team);
     const size_t b_params = al256(sizeof(Params) * (size_t)o.max_batch_graphs);
     const size_t b_lists = al256(sizeof(int32_t) * s.lists_cap);
     const size_t b_ctrl = al256(sizeof(Ctrl) * (size_t)o.max_batch_graphs);
     char* base = nullptr;
     if (cudaMalloc((void**)&base, b_params + b_lists + b_ctrl) != cudaSuccess ||
         cudaMallocHost((void**)&s.h_ctrl, sizeof(Ctrl) * (size_t)o.max_batch_graphs) != cudaSuccess ||
+        cudaMallocHost((void**)&s.h_done, sizeof(int32_t) * (size_t)o.max_batch_graphs) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&s.m_ctrl, s.h_ctrl, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&s.m_done, s.h_done, 0) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
       if (base) cudaFree(base);
@@ -466,15 +500,19 @@ int ipgc_server_create(ipgc_server** out, int device, const ipgc_server_options*
   return IPGC_OK;
 }
 
-int ipgc_server_submit(ipgc_server* S, const int32_t* h_rowptr, const int32_t* h_col, int32_t n,
-                       int64_t nnz, uint64_t* ticket) {
+}  // extern "C"
+
+namespace {
+
+int submit_impl(ipgc_server* S, const int32_t* h_rowptr, const int32_t* h_col, int32_t n,
+                int64_t nnz, uint64_t* ticket, bool by_ref) {
   if (!S || !ticket || n < 0 || nnz < 0 || nnz > INT32_MAX || n == INT32_MAX) return IPGC_ERR_INVALID;
   if ((n > 0 && !h_rowptr) || (nnz > 0 && !h_col) || (nnz > 0 && n == 0)) return IPGC_ERR_INVALID;
   if (n > 0 && (h_rowptr[0] != 0 || (int64_t)h_rowptr[n] != nnz)) return IPGC_ERR_INVALID;
   if (S->opt.batch.base.validate &&
       ipgc_validate_csr(nullptr, h_rowptr, h_col, n, nnz, 0, nullptr) != IPGC_OK)
     return IPGC_ERR_INVALID;
-  const size_t hb = host_bytes(n, nnz);
+  const size_t hb = by_ref ? al256(4 * (size_t)(n > 0 ? n : 1)) : host_bytes(n, nnz);
   const size_t db = dev_layout(n, nnz, S->t1, S->chunk).total;
   if (hb > S->host.cap() || db > S->dev.cap()) return IPGC_ERR_TOO_LARGE;
   size_t h_off = 0;
@@ -491,14 +529,21 @@ int ipgc_server_submit(ipgc_server* S, const int32_t* h_rowptr, const int32_t* h
     r.nnz = nnz;
     r.h_off = h_off;
     r.h_bytes = hb;
+    r.h_colors = by_ref ? 0
+                        : al256(4 * ((size_t)n + 1)) + al256(4 * (size_t)(nnz > 0 ? nnz : 1));
     r.d_bytes = db;
     r.st = St::Pending;
     r.t_submit = Clock::now();
+    if (by_ref) {
+      r.ref_rowptr = h_rowptr;
+      r.ref_col = h_col;
+    }
   }
-  // copy the graph into staging outside the lock (the slot is ours)
-  char* hb_base = S->h_arena + h_off;
-  if (n > 0) std::memcpy(hb_base, h_rowptr, 4 * ((size_t)n + 1));
-  if (nnz > 0) std::memcpy(hb_base + al256(4 * ((size_t)n + 1)), h_col, 4 * (size_t)nnz);
+  if (!by_ref) {  // copy the graph into staging outside the lock (the block is ours)
+    char* hb_base = S->h_arena + h_off;
+    if (n > 0) std::memcpy(hb_base, h_rowptr, 4 * ((size_t)n + 1));
+    if (nnz > 0) std::memcpy(hb_base + al256(4 * ((size_t)n + 1)), h_col, 4 * (size_t)nnz);
+  }
   {
     std::lock_guard<std::mutex> lk(S->mu);
     Request& r = S->reqs[t];
@@ -518,6 +563,20 @@ int ipgc_server_submit(ipgc_server* S, const int32_t* h_rowptr, const int32_t* h
   return IPGC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int ipgc_server_submit(ipgc_server* S, const int32_t* h_rowptr, const int32_t* h_col, int32_t n,
+                       int64_t nnz, uint64_t* ticket) {
+  return submit_impl(S, h_rowptr, h_col, n, nnz, ticket, false);
+}
+
+int ipgc_server_submit_ref(ipgc_server* S, const int32_t* h_rowptr, const int32_t* h_col,
+                           int32_t n, int64_t nnz, uint64_t* ticket) {
+  return submit_impl(S, h_rowptr, h_col, n, nnz, ticket, true);
+}
+
 int ipgc_server_poll(ipgc_server* S, uint64_t ticket, int32_t* h_colors, ipgc_stats* stats,
                      int64_t* latency_ns) {
   if (!S) return IPGC_ERR_INVALID;
@@ -527,11 +586,8 @@ int ipgc_server_poll(ipgc_server* S, uint64_t ticket, int32_t* h_colors, ipgc_st
   Request& r = it->second;
   if (r.st != St::Done && r.st != St::Failed) return IPGC_PENDING;
   const int err = r.st == St::Done ? IPGC_OK : (r.err != IPGC_OK ? r.err : IPGC_ERR_CUDA);
-  if (err == IPGC_OK && h_colors && r.n > 0) {
-    const char* src = S->h_arena + r.h_off + al256(4 * ((size_t)r.n + 1)) +
-                      al256(4 * (size_t)(r.nnz > 0 ? r.nnz : 1));
-    std::memcpy(h_colors, src, 4 * (size_t)r.n);
-  }
+  if (err == IPGC_OK && h_colors && r.n > 0)
+    std::memcpy(h_colors, S->h_arena + r.h_off + r.h_colors, 4 * (size_t)r.n);
   if (stats) *stats = r.stats;
   if (latency_ns)
     *latency_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(r.t_done - r.t_submit).count();

@@ -47,6 +47,8 @@ SIGNATURES = {
     "ipgc_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ServerOptions)]),
     "ipgc_server_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "ipgc_server_submit_ref": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64,
+                                              ctypes.POINTER(ctypes.c_uint64)]),
     "ipgc_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(ipgc.Stats),
                                         ctypes.POINTER(ctypes.c_int64)]),
     "ipgc_server_next_done": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64]),
@@ -98,6 +100,20 @@ class Server:
                                       rowptr.size - 1, col.size, ctypes.byref(t))
         if rc != ipgc.IPGC_OK:
             raise ipgc.IpgcError(rc, "ipgc_server_submit")
+        self._n[t.value] = rowptr.size - 1
+        return t.value
+
+    def submit_ref(self, rowptr: np.ndarray, col: np.ndarray) -> int:
+        """Queue a graph by reference: the arrays (int32, contiguous, ideally in
+        pinned memory) must stay alive and unchanged until the ticket completes."""
+        assert rowptr.dtype == np.int32 and col.dtype == np.int32
+        assert rowptr.flags.c_contiguous and col.flags.c_contiguous
+        t = ctypes.c_uint64(0)
+        rc = lib().ipgc_server_submit_ref(self.handle, rowptr.ctypes.data,
+                                          col.ctypes.data if col.size else None,
+                                          rowptr.size - 1, col.size, ctypes.byref(t))
+        if rc != ipgc.IPGC_OK:
+            raise ipgc.IpgcError(rc, "ipgc_server_submit_ref")
         self._n[t.value] = rowptr.size - 1
         return t.value
 

@@ -74,12 +74,12 @@ def mixed_batch():
     "kw",
     [
         dict(),
-        dict(team_min_nnz=0),                    # every graph on a team of 8
-        dict(team_min_nnz=0, team_size=2),
-        dict(team_min_nnz=50_000, team_size=16),
-        dict(team_min_nnz=1 << 40),              # every graph on one CTA
+        dict(nnz_per_cta=1),                     # every graph on a grid-sized team
+        dict(nnz_per_cta=1, max_team=2),
+        dict(nnz_per_cta=5_000, max_team=16),    # teams of 1..16 CTAs
+        dict(nnz_per_cta=1 << 40),               # every graph on one CTA
         dict(mode="data"),
-        dict(mode="topo", team_min_nnz=100_000),
+        dict(mode="topo", nnz_per_cta=20_000),
         dict(block_size=512, chunk=256, t1=8),
     ],
 )
@@ -101,7 +101,7 @@ def test_degenerate_graphs_in_a_batch(ctx):
     star = graphgen.from_edges(3000, np.zeros(2999, np.int32), np.arange(1, 3000, dtype=np.int32))
     graphs = [edgeless, empty, one, clique, graphgen.rmat(12, 8, seed=5), empty, star]
     bt = make_batch(graphs)
-    colors, st = run_batch(ctx, bt, team_min_nnz=4000)
+    colors, st = run_batch(ctx, bt, nnz_per_cta=2000, max_team=8)
     check_against_oracle(bt, colors, st)
     assert st["rounds"][1] == 0 and st["rounds"][5] == 0
 
@@ -110,7 +110,7 @@ def test_batch_equals_single_graph_calls(ctx):
     import torch
 
     bt = graphgen.batch(16, seed=7, nmin=2_000, nmax=60_000)
-    colors, st = run_batch(ctx, bt, team_min_nnz=100_000)
+    colors, st = run_batch(ctx, bt, nnz_per_cta=30_000)
     no = bt["node_off"]
     for g in range(16):
         rp, cl = graphgen.batch_graph(bt, g)
@@ -144,7 +144,7 @@ def test_autotuners_keep_colours(ctx):
     dcl = torch.from_numpy(bt["col_cat"]).cuda()
     out = torch.empty(int(bt["node_off"][-1]), dtype=torch.int32, device="cuda")
     o, ms = batched.autotune(ctx, bt["node_off"], bt["edge_off"], drp, dcl, out, sample_graphs=12)
-    assert ms > 0 and o.base.chunk in (512, 1024, 2048) and o.team_size in (2, 4, 8, 16)
+    assert ms > 0 and o.base.chunk in (0, 512, 1024, 2048) and o.max_team in (0, 4, 16, 64)
     colors, st = batched.color_batched(ctx, bt["node_off"], bt["edge_off"], drp, dcl, opts=o)
     check_against_oracle(bt, colors.cpu().numpy(), st)
     # single-graph tuner

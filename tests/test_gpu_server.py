@@ -118,3 +118,63 @@ def test_errors_and_ticket_reuse(graphs):
     for rp2, cl2 in gs[:10]:
         srv.submit(rp2, cl2)
     srv.close()
+
+
+def test_submission_by_reference(graphs):
+    import torch
+
+    from paper_1912_01478_gb300 import server
+
+    gs, refs = graphs
+    srv = server.Server(0, server.options(inflight=2, max_batch_graphs=16))
+    keep = []
+    tickets = []
+    for rp, cl in gs:
+        prp = torch.from_numpy(rp).pin_memory()
+        pcl = torch.from_numpy(cl).pin_memory()
+        keep.append((prp, pcl))
+        tickets.append(srv.submit_ref(prp.numpy(), pcl.numpy()))
+    for t, ref in zip(tickets, refs):
+        while (r := srv.poll(t)) is None:
+            time.sleep(0.0005)
+        check(r, ref)
+    srv.close()
+
+
+def test_small_requests_finish_before_a_large_one_in_the_same_launch():
+    # with one batch slot, a first request keeps the slot busy while a large
+    # graph (on a small team) and many tiny graphs queue up; they then share
+    # one launch, and each tiny request completes as soon as its own CTA is
+    # done, before the large one, not when the launch ends
+    from paper_1912_01478_gb300 import server
+
+    blocker = graphgen.rmat(18, 16, seed=10)
+    big = graphgen.rmat(18, 16, seed=11)
+    tiny = pool(64, seed=12, nmax=1_500)
+    ref_blocker = oracle.color(*blocker, trace=False)
+    ref_big = oracle.color(*big, trace=False)
+    refs = [oracle.color(rp, cl, trace=False) for rp, cl in tiny]
+    o = server.options(inflight=1, max_batch_graphs=256)
+    o.batch.max_team = 4
+    srv = server.Server(0, o)
+    t0 = srv.submit(*blocker)
+    time.sleep(0.01)  # let the blocker launch
+    tb = srv.submit(*big)
+    ts = [srv.submit(rp, cl) for rp, cl in tiny]
+    order = []
+    done = {}
+    deadline = time.time() + 120
+    while len(done) < len(ts) + 2 and time.time() < deadline:
+        t = srv.next_done(timeout_s=1.0)
+        if t is not None:
+            order.append(t)
+            done[t] = srv.poll(t)
+    assert len(done) == len(ts) + 2
+    check(done[t0], ref_blocker)
+    check(done[tb], ref_big)
+    for t, ref in zip(ts, refs):
+        check(done[t], ref)
+    c = srv.counters()
+    srv.close()
+    assert c.batches == 2 and c.max_batch == len(ts) + 1
+    assert order[0] == t0 and order[-1] == tb
