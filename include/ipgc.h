@@ -126,7 +126,17 @@ typedef struct ipgc_options {
   float policy_margin;    /* IPGC_MODE_LEARNED: when the network's probability p of "topology
                              is faster" has |p - 0.5| < policy_margin, or no network is
                              loaded, the threshold rule decides; default 0.05 */
-  int32_t reserved2;
+  int32_t filter_degree;  /* neighbour filtering: once the worklist is small (filter_start),
+                             a node of degree > max(filter_degree, chunk, t1) keeps the list
+                             of its still-active neighbours and a bitmap of the colours of
+                             its finalised ones, so later rounds read only the active part
+                             of its row (same colours; more workspace: about 8 bytes per
+                             entry). 0 = default 1024; < 0 = off. Single-graph entry points
+                             only; used while every colour is <= 2047. */
+  float filter_start;     /* filtering starts at the first round r >= 3 whose worklist has at
+                             most filter_start * n nodes of mean degree above the filter
+                             degree; 0 = default 1/160 */
+  int32_t reserved3;
 } ipgc_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -87,34 +87,50 @@ int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
 
 // Workspace of one colouring, every array 256-byte aligned:
 //   tent[n]; low-degree worklists [2 parities][n]; work items (int4) of the
-//   high-degree nodes [2 parities + static][item_cap]; merge state of nodes
-//   with several items: bits [gcap][kGWords], done_a, done_d, flag [gcap].
+//   high-degree nodes [2 parities + static][item_cap]; per-node state of
+//   nodes with several items or with filtering: bits [gcap][kGWords],
+//   done_a, done_d, flag [gcap]; with neighbour filtering, the filtered lists
+//   [2 parities][nnz], their counts (int2) [2 parities][gcap] and the work
+//   items of filtered nodes [2 parities][item_cap].
 // A node of degree > t1 has more than t1 entries, so at most nnz / (t1 + 1)
 // exist, with at most nnz / chunk + (their number) items; a node with several
-// items has more than `chunk` entries.
+// items has more than `chunk` entries and a filtered one more than filt_deg.
 struct WsLayout {
-  size_t a4n, items_bytes, gbits_bytes, gint_bytes, total;
+  size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, total;
 };
 
 using ipgc::effective_chunk;
 using ipgc::effective_t1;
 
-WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk) {
+// Degree above which a node is filtered (INT32_MAX: off); at least the
+// chunk, so every such node has several work items and a merge-state slot.
+int effective_filt_deg(const ipgc_options& o) {
+  if (o.filter_degree < 0) return INT32_MAX;
+  const int f = o.filter_degree > 0 ? o.filter_degree : ipgc::kDefaultFiltDeg;
+  const int lo = effective_chunk(o) > effective_t1(o) ? effective_chunk(o) : effective_t1(o);
+  return f > lo ? f : lo;
+}
+
+WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk, int filt_deg) {
   WsLayout L;
   L.a4n = align256((size_t)n * sizeof(int32_t));
   int64_t nbig = nnz / ((int64_t)t1 + 1);
   if (nbig > n) nbig = n;
   const int64_t item_cap = nnz / chunk + nbig + 1;
+  const bool filt = filt_deg != INT32_MAX;
   const int64_t gcap = nnz / ((int64_t)chunk + 1) + 1;
   L.items_bytes = align256((size_t)item_cap * sizeof(int4));
   L.gbits_bytes = align256((size_t)gcap * ipgc::kGWords * sizeof(uint32_t));
   L.gint_bytes = align256((size_t)gcap * sizeof(int32_t));
-  L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes;
+  L.alist_bytes = filt ? align256((size_t)nnz * sizeof(int32_t)) : 0;
+  L.flen_bytes = filt ? align256((size_t)gcap * sizeof(int2)) : 0;
+  L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes +
+            2 * L.alist_bytes + 2 * L.flen_bytes + (filt ? 2 * L.items_bytes : 0);
   return L;
 }
 
 size_t ws_bytes_for(int32_t n, int64_t nnz, const ipgc_options& o) {
-  return ws_layout(n, nnz, effective_t1(o), effective_chunk(o)).total;
+  return ws_layout(n, nnz, effective_t1(o), effective_chunk(o), effective_filt_deg(o)).total;
 }
 
 int ensure_ws(ipgc_ctx* ctx, int32_t n, int64_t nnz, const ipgc_options& o) {
@@ -151,7 +167,8 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.color = colors;
   p.t1 = effective_t1(o);
   p.chunk = effective_chunk(o);
-  const WsLayout L = ws_layout(n, nnz, p.t1, p.chunk);
+  p.filt_deg = effective_filt_deg(o);
+  const WsLayout L = ws_layout(n, nnz, p.t1, p.chunk, p.filt_deg);
   const size_t a = L.a4n;
   char* w = ctx->ws;
   p.tent = (int32_t*)w;
@@ -173,6 +190,24 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.done_d = (int32_t*)w;
   w += L.gint_bytes;
   p.flag = (int32_t*)w;
+  w += L.gint_bytes;
+  if (L.alist_bytes) {
+    p.alist[0] = (int32_t*)w;
+    w += L.alist_bytes;
+    p.alist[1] = (int32_t*)w;
+    w += L.alist_bytes;
+    p.flen[0] = (int2*)w;
+    w += L.flen_bytes;
+    p.flen[1] = (int2*)w;
+    w += L.flen_bytes;
+    p.fitems[0] = (int4*)w;
+    w += L.items_bytes;
+    p.fitems[1] = (int4*)w;
+    // hand over to filtering once |WL| <= filter_start * n
+    const double fs = o.filter_start > 0 ? (double)o.filter_start : ipgc::kDefaultFiltStart;
+    const double hw = fs * (double)n;
+    p.handoff_wl = hw >= 1.0 ? (int64_t)hw : 1;
+  }
   p.ctrl = ctx->d_ctrl;
   p.trace = o.trace;
   p.fin = o.fin_round;
@@ -219,7 +254,8 @@ int run_validate(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32
   return *ctx->h_err ? IPGC_ERR_INVALID : IPGC_OK;
 }
 
-int run_hostloop(ipgc_ctx* ctx, const Params& p, int bs, int blocks, cudaStream_t s) {
+int run_hostloop(ipgc_ctx* ctx, const Params& p0, int bs, int blocks, cudaStream_t s) {
+  Params p = p0;
   IPGC_CUDA(ctx, ipgc::launch_round1(p, bs, blocks, s));
   int r = 2;
   for (;; ++r) {
@@ -250,6 +286,12 @@ int run_hostloop(ipgc_ctx* ctx, const Params& p, int bs, int blocks, cudaStream_
                             c.maxc, f);
       const float pr = 1.0f / (1.0f + std::exp(-ipgc::mlp_logit_host(ctx->h_mlp.data(), f)));
       if (std::fabs(pr - 0.5f) >= p.mlp_margin) mode = pr > 0.5f ? IPGC_MODE_TOPO : IPGC_MODE_DATA;
+    }
+    if (p.filt_r0 == 0 && ipgc::handoff_now(p, r, total, ctx->h_ctrl->dsum[par], ctx->h_ctrl->maxc)) {
+      // hand over to neighbour filtering: list counts start at zero
+      const WsLayout L = ws_layout(p.n, p.nnz, p.t1, p.chunk, p.filt_deg);
+      IPGC_CUDA(ctx, cudaMemsetAsync(p.flen[0], 0, 2 * L.flen_bytes, s));
+      p.filt_r0 = r;
     }
     IPGC_CUDA(ctx, ipgc::launch_assign(p, bs, blocks, r, mode, s));
     IPGC_CUDA(ctx, ipgc::launch_detect(p, bs, blocks, r, mode, s));

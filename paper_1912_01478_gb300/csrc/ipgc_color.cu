@@ -43,6 +43,15 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(Params p
   color_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
 }
 
+// The rounds after the hand-over to neighbour filtering (enqueued right after
+// persistent_kernel; returns at once when no hand-over happened).
+template <int BS>
+__global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_filt_kernel(Params p) {
+  __shared__ Smem<BS> sm;
+  smem_clear<BS>(sm);
+  continue_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
+}
+
 // ------------------------------------------------------ host-loop kernels --
 
 template <int BS>
@@ -56,7 +65,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) round1_kernel(Params p) {
   if (blockIdx.x == 0 && threadIdx.x == 0) trace_round1(p, t0);
 }
 
-template <int BS>
+template <int BS, bool FILT>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) assign_kernel(Params p, int r, int mode) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
@@ -68,10 +77,10 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) assign_kernel(Params p, in
   const int64_t total = (int64_t)rv.nsmall + rv.nbig;
   const Team tm{(int)blockIdx.x, (int)gridDim.x};
   round_begin(p, rv, r, total, tm);
-  assign_phase<BS>(p, sm, rv, tm);
+  assign_phase<BS, FILT>(p, sm, rv, tm);
 }
 
-template <int BS>
+template <int BS, bool FILT>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) detect_kernel(Params p, int r, int mode) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
@@ -80,7 +89,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) detect_kernel(Params p, in
   RoundView rv = read_round(p, r);
   rv.mode = mode;
   PhaseAcc acc;
-  detect_phase<BS>(p, sm, rv, acc, Team{(int)blockIdx.x, (int)gridDim.x});
+  detect_phase<BS, FILT>(p, sm, rv, acc, Team{(int)blockIdx.x, (int)gridDim.x});
   phase_commit<BS>(p, sm, acc, rv.par ^ 1);
 }
 
@@ -135,20 +144,40 @@ __global__ void validate_kernel(const int32_t* __restrict__ rowptr, const int32_
 
 // ------------------------------------------------------------ host launch --
 
-cudaError_t occupancy_persistent(int bs, int* blocks_per_sm) {
+// The phases with neighbour filtering (FILT) are separate instantiations, so
+// the kernels without it keep their register budget.
+template <class F>
+cudaError_t with_block_filt(int bs, bool filt, F f) {
   return with_block(bs, [&](auto B) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                         persistent_kernel<decltype(B)::value>,
-                                                         decltype(B)::value, 0);
+    return filt ? f(B, std::true_type()) : f(B, std::false_type());
   });
+}
+
+cudaError_t occupancy_persistent(int bs, int* blocks_per_sm) {
+  // the smaller of the two kernels' occupancies
+  int a = 0, b = 0;
+  cudaError_t e = with_block(bs, [&](auto B) {
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, persistent_kernel<decltype(B)::value>, decltype(B)::value, 0);
+    if (r == cudaSuccess)
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &b, persistent_filt_kernel<decltype(B)::value>, decltype(B)::value, 0);
+    return r;
+  });
+  *blocks_per_sm = a < b ? a : b;
+  return e;
 }
 
 cudaError_t launch_persistent(const Params& p, int bs, int blocks, cudaStream_t s) {
   return with_block(bs, [&](auto B) {
     Params pp = p;
     void* args[] = {&pp};
-    return cudaLaunchCooperativeKernel((const void*)persistent_kernel<decltype(B)::value>,
-                                       dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)persistent_kernel<decltype(B)::value>,
+                                                dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+    if (e == cudaSuccess && p.handoff_wl > 0)
+      e = cudaLaunchCooperativeKernel((const void*)persistent_filt_kernel<decltype(B)::value>,
+                                      dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+    return e;
   });
 }
 
@@ -160,15 +189,17 @@ cudaError_t launch_round1(const Params& p, int bs, int blocks, cudaStream_t s) {
 }
 
 cudaError_t launch_assign(const Params& p, int bs, int blocks, int round, int mode, cudaStream_t s) {
-  return with_block(bs, [&](auto B) {
-    assign_kernel<decltype(B)::value><<<blocks, decltype(B)::value, 0, s>>>(p, round, mode);
+  return with_block_filt(bs, p.filt_r0 > 0, [&](auto B, auto F) {
+    assign_kernel<decltype(B)::value, decltype(F)::value>
+        <<<blocks, decltype(B)::value, 0, s>>>(p, round, mode);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_detect(const Params& p, int bs, int blocks, int round, int mode, cudaStream_t s) {
-  return with_block(bs, [&](auto B) {
-    detect_kernel<decltype(B)::value><<<blocks, decltype(B)::value, 0, s>>>(p, round, mode);
+  return with_block_filt(bs, p.filt_r0 > 0, [&](auto B, auto F) {
+    detect_kernel<decltype(B)::value, decltype(F)::value>
+        <<<blocks, decltype(B)::value, 0, s>>>(p, round, mode);
     return cudaGetLastError();
   });
 }

@@ -24,6 +24,9 @@ constexpr int kDefaultChunk = 1024;
 constexpr int kMinChunk = 32;
 constexpr int kMaxChunk = 4096;
 constexpr int kGWords = 64;      // per-warp / per-node bitmap: colours 1..2048
+constexpr int kFiltMaxC = 32 * kGWords - 2;  // neighbour filtering while maxc <= this
+constexpr int kDefaultFiltDeg = 1024;
+constexpr double kDefaultFiltStart = 1.0 / 160;  // hand over once |WL| <= n / 160
 constexpr int kStageSmall = 128; // per-warp staging of low-degree pushes
 constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
 
@@ -43,7 +46,10 @@ struct Ctrl {
   unsigned long long t_start, t_end;
   unsigned long long t_prev_assign, t_prev_detect;  // previous round's phase times
   int32_t ctas_done;               // team CTAs that have published their share of the result
-  int32_t pad[7];
+  int32_t maxc_start[2];           // largest committed colour at the start of a round, per parity
+  int32_t ficnt[2];                // work items of the worklist's filtered nodes, per parity
+  int32_t handoff_round;           // first round of neighbour filtering (0: none)
+  int32_t pad[2];
 };
 
 struct Params {
@@ -76,6 +82,21 @@ struct Params {
   uint32_t bar_extra; // tests only: phantom CTAs every grid barrier waits for
   int32_t col_vec;    // col is 16-byte aligned: int4 loads and bulk L2 prefetches allowed
   float mlp_margin;   // learned policy: threshold rule when |p - 0.5| < margin
+  // Neighbour filtering (alist[0] == nullptr: off). From the hand-over round
+  // r0 on, a node of degree > filt_deg (>= chunk, so it has a merge-state
+  // slot) that is active in round r > r0 reads only the list of its
+  // neighbours still active in round r - 1, kept in alist[r & 1] inside the
+  // node's own row range [rowptr[v], rowptr[v + 1]): lower IDs from the front,
+  // higher IDs from the back, their counts in flen[r & 1][gslot]; in round r0
+  // it reads the row itself. Colours of its finalised neighbours accumulate in
+  // gbits[gslot] across rounds. Used in round r iff every colour committed
+  // before round r - 1 is <= kFiltMaxC, so the bitmap holds every colour.
+  int32_t* alist[2];
+  int2* flen[2];
+  int4* fitems[2];    // work items of filtered nodes, per parity (as items[])
+  int32_t filt_deg;
+  int32_t filt_r0;    // host-loop driver: the hand-over round once reached (0: not yet)
+  int64_t handoff_wl; // hand over when |WL| <= handoff_wl (0: never)
   // Optional result publication into host-mapped pinned memory (nullptr:
   // none). When a graph is done its team copies the colours to out_colors
   // and the control block to out_ctrl, then sets *out_done = 1, so the host
@@ -84,6 +105,16 @@ struct Params {
   Ctrl* out_ctrl;
   int32_t* out_done;
 };
+
+// Neighbour filtering takes over at the first round r >= 3 whose worklist
+// has at most handoff_wl nodes of mean degree > filt_deg (by then most of
+// their neighbours are finalised), while every colour fits the bitmap.
+// Evaluated by the kernel and by the host-loop driver alike.
+__host__ __device__ inline bool handoff_now(const Params& p, int r, int64_t total,
+                                            unsigned long long dsum, int maxc) {
+  return p.handoff_wl > 0 && r >= 3 && total <= p.handoff_wl &&
+         dsum > (unsigned long long)total * (unsigned long long)p.filt_deg && maxc <= kFiltMaxC;
+}
 
 // ------------------------------------------------------- learned policy --
 
@@ -306,6 +337,24 @@ __device__ __forceinline__ void items_push(ItemStage& st, int v, int cnt, int gs
   for (int j = 0; j < cnt; ++j) st.buf[st.fill + excl + j] = make_int4(v, j, gslot, cnt);
   __syncwarp();
   st.fill += tot;
+}
+
+// items_push without staging: one warp-aggregated reservation per call.
+__device__ __forceinline__ void items_push_direct(int v, int cnt, int gslot, int4* list,
+                                                  int32_t* counter) {
+  const int lane = lane_id();
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int tot = __shfl_sync(FULL, incl, 31);
+  if (tot == 0) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(counter, tot);
+  base = __shfl_sync(FULL, base, 0) + incl - cnt;
+  for (int j = 0; j < cnt; ++j) list[base + j] = make_int4(v, j, gslot, cnt);
 }
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {

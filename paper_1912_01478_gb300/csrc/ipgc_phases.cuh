@@ -23,7 +23,8 @@ struct Smem {
   unsigned wbits[W][kGWords];       // per warp: bitmap of colours 1..2048 (work items)
   int32_t stage_s[W][kStageSmall];  // staged pushes: low-degree losers
   int4 stage_i[W][kStageItems];     // staged pushes: work items of high-degree losers
-  int4 stage_t[W][kStageItems];     // staged pushes: static work items (round 1)
+  int4 stage_t[W][kStageItems];     // staged pushes: static work items (round 1),
+                                    // items of filtered nodes (conflict steps)
   unsigned long long red64[W];
   int red[W];
   int mode_b;  // broadcast of the round's mode (learned policy)
@@ -128,7 +129,7 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm) {
     const bool big = valid && bucket_of(d, p.t1) == B_BIG;
     stage_push(ss, kStageSmall, lose && !big, v, p.wl[0], &c->cnt[0][B_SMALL]);
     const int nch = big ? num_chunks(d, p.chunk) : 0;
-    const bool multi = nch > 1;
+    const bool multi = nch > 1;  // (every node that can be filtered is one of them)
     const unsigned mm = __ballot_sync(FULL, multi);
     int gslot = -1;
     if (mm) {
@@ -310,6 +311,28 @@ __device__ __forceinline__ void load_window(const Params& p, int64_t a, int64_t 
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         u[4 * h + j] = (q + j >= lo && q + j < hi) ? ld_ro(p.col + q + j) : none;
+    }
+  }
+}
+
+// The same over a neighbour list written during the launch (16-byte aligned
+// base; read through L2, not the read-only path).
+__device__ __forceinline__ void load_window_rw(const int32_t* arr, int64_t a, int64_t lo, int64_t hi,
+                                               int none, int (&u)[kGather]) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t q = a + 128 * h + 4 * lane;
+    if (q >= lo && q + 3 < hi) {
+      const int4 x = ld_cg4(reinterpret_cast<const int4*>(arr + q));
+      u[4 * h + 0] = x.x;
+      u[4 * h + 1] = x.y;
+      u[4 * h + 2] = x.z;
+      u[4 * h + 3] = x.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        u[4 * h + j] = (q + j >= lo && q + j < hi) ? ld_cg(arr + q + j) : none;
     }
   }
 }
@@ -500,6 +523,240 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
   }
 }
 
+// ------------------------------------------------------ neighbour filtering --
+//
+// Filtering starts at round r0 (the hand-over round, see continue_graph).
+// A filtered node v reads in round r the list of its neighbours that were
+// active in round r - 1 (in round r0: its whole row). A neighbour found
+// committed is finalised for good: its colour goes into v's persistent
+// bitmap and it leaves the list. The others are written to the list of round
+// r + 1, which is then exactly v's set of neighbours active in round r: the
+// only ones the conflict step can find a clash with (a finalised neighbour's
+// colour is excluded from tent[v]). The colours, rounds and worklists are
+// those of rescanning the whole row; only the entries read shrink.
+
+// Work items of filtered node v in round r: chunks of its list.
+__device__ __forceinline__ int filt_items(const Params& p, int round, int r0, int gslot, int d) {
+  if (round == r0) return num_chunks(d, p.chunk);
+  const int2 L = __ldcg(p.flen[round & 1] + gslot);
+  return max(1, num_chunks(L.x + L.y, p.chunk));
+}
+
+// Entries [lo, hi) of v's current list (absolute indexes into src; src is
+// col in round r0): colours of committed neighbours into pm (1..32,
+// lane-private) and wb (33..2048); active neighbours appended to the next
+// list dst within v's row range [s, s + d), lower IDs from the front and
+// higher IDs from the back, counted in *nlen.
+__device__ __forceinline__ void filt_assign_range(const Params& p, const int32_t* src, bool from_col,
+                                                  int64_t lo, int64_t hi, int v, int64_t s, int d,
+                                                  int32_t* dst, int2* nlen, unsigned& pm,
+                                                  unsigned* wb) {
+  const int lane = lane_id();
+  const uint64_t pol = l2_keep_policy();
+  int64_t a = lo & ~int64_t(3);
+  int u[kGather];
+  if (from_col)
+    load_window(p, a, lo, hi, -1, u);
+  else
+    load_window_rw(src, a, lo, hi, -1, u);
+  for (; a < hi; a += kWindow) {
+    int un[kGather];
+    const bool more = a + kWindow < hi;
+    if (more) {
+      if (from_col)
+        load_window(p, a + kWindow, lo, hi, -1, un);
+      else
+        load_window_rw(src, a + kWindow, lo, hi, -1, un);
+    }
+    int cc[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) cc[q] = u[q] >= 0 ? ld_keep(p.color + u[q], pol) : 0;
+    int klo = 0, khi = 0;
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      if (u[q] < 0) continue;
+      const int c = cc[q];
+      if (c == 0) {
+        if (u[q] < v)
+          ++klo;
+        else
+          ++khi;
+      } else if (c <= 32) {
+        pm |= 1u << (c - 1);
+      } else if (c <= 32 * kGWords) {
+        atomicOr(&wb[(c - 1) >> 5], 1u << ((c - 1) & 31));
+      }
+    }
+    int xlo = klo, xhi = khi;  // inclusive prefix sums over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ylo = __shfl_up_sync(FULL, xlo, o), yhi = __shfl_up_sync(FULL, xhi, o);
+      if (lane >= o) {
+        xlo += ylo;
+        xhi += yhi;
+      }
+    }
+    const int tlo = __shfl_sync(FULL, xlo, 31), thi = __shfl_sync(FULL, xhi, 31);
+    if (tlo | thi) {
+      int blo = 0, bhi = 0;
+      if (lane == 0) {
+        if (tlo) blo = atomicAdd(&nlen->x, tlo);
+        if (thi) bhi = atomicAdd(&nlen->y, thi);
+      }
+      int olo = __shfl_sync(FULL, blo, 0) + xlo - klo;
+      int ohi = __shfl_sync(FULL, bhi, 0) + xhi - khi;
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) {
+        if (u[q] < 0 || cc[q] != 0) continue;
+        if (u[q] < v)
+          dst[s + olo++] = u[q];
+        else
+          dst[s + d - 1 - ohi++] = u[q];
+      }
+    }
+    if (more) {
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) u[q] = un[q];
+    }
+  }
+}
+
+// Assignment step for work item c of nch of filtered node v in round r: the
+// item's share of the list, then the persistent bitmap gives tent[v].
+__device__ __forceinline__ void item_assign_filtered(const Params& p, unsigned* wb, int v, int s,
+                                                     int d, int c, int nch, int gslot, int round,
+                                                     int r0, int maxc) {
+  const int lane = lane_id();
+  const int nb = (round + 1) & 1;
+  int32_t* dst = p.alist[nb];
+  int2* nlen = p.flen[nb] + gslot;
+  unsigned pm = 0;
+  if (round == r0) {  // the first filtered round builds the list from the row
+    const int b = c * p.chunk, e = min(d, b + p.chunk);
+    filt_assign_range(p, p.col, true, (int64_t)s + b, (int64_t)s + e, v, s, d, dst, nlen, pm, wb);
+  } else {
+    // the list: [0, L.x) at s + k, [L.x, L.x + L.y) at s + d - L.y + (k - L.x)
+    const int32_t* src = p.alist[round & 1];
+    const int2 L = __ldcg(p.flen[round & 1] + gslot);
+    const int b = c * p.chunk, e = min(L.x + L.y, b + p.chunk);
+    if (b < L.x)
+      filt_assign_range(p, src, false, (int64_t)s + b, (int64_t)s + min(e, L.x), v, s, d, dst,
+                        nlen, pm, wb);
+    if (e > L.x) {
+      const int64_t h0 = (int64_t)s + d - L.y - L.x;
+      filt_assign_range(p, src, false, h0 + max(b, L.x), h0 + e, v, s, d, dst, nlen, pm, wb);
+    }
+  }
+  pm = __reduce_or_sync(FULL, pm);
+  __syncwarp();
+  const int lim = min(d, maxc) + 1;  // <= 2048 while filtering
+  const int nw = (lim + 31) >> 5;
+  uint32_t* g = p.gbits + (size_t)gslot * kGWords;
+  unsigned nv[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    const unsigned w = (i == 0 ? pm : 0u) | wb[i];
+    nv[h] = w ? (atomicOr(&g[i], w) | w) : (nch == 1 ? __ldcg(g + i) : 0u);
+  }
+  __syncwarp();
+  wb[lane] = 0;
+  wb[lane + 32] = 0;
+  __syncwarp();
+  if (nch == 1) {
+    const int t = first_free_64(nw, [&](int i) { return i >= 32 ? nv[1] : nv[0]; });
+    if (lane == 0) p.tent[v] = t;
+    return;
+  }
+  __threadfence();
+  __syncwarp();
+  int last = 0;
+  if (lane == 0) last = atomicAdd(&p.done_a[gslot], 1) == nch - 1;
+  last = __shfl_sync(FULL, last, 0);
+  if (last) {  // every other item of v has merged its bits
+    __threadfence();
+    const int t = first_free_64(nw, [&](int i) { return __ldcg(g + i); });
+    if (lane == 0) {
+      p.tent[v] = t;
+      p.done_a[gslot] = 0;
+    }
+  }
+}
+
+// Conflict step for work item c of nch of filtered node v in round r: its
+// share of v's lower-ID active neighbours (the front part of the list the
+// assignment step wrote). The warp that finishes v's last item commits v or
+// pushes its items for round r + 1 (shaped for filtering when filt_next).
+__device__ __forceinline__ void item_detect_filtered(const Params& p, ItemStage& lstage,
+                                                     ItemStage& fstage, int v, int s, int d, int c,
+                                                     int nch, int gslot, int nxt, PhaseAcc& acc,
+                                                     int round, bool filt_next) {
+  const int lane = lane_id();
+  const uint64_t pol = l2_keep_policy();
+  const int t = ld_cg(p.tent + v);
+  const int nb = (round + 1) & 1;
+  const int2 L1 = __ldcg(p.flen[nb] + gslot);
+  const int32_t* lst = p.alist[nb];
+  const int64_t lo = (int64_t)s + (int64_t)L1.x * c / nch;
+  const int64_t hi = (int64_t)s + (int64_t)L1.x * (c + 1) / nch;
+  bool hit = false;
+  if (lo < hi) {
+    int64_t a = lo & ~int64_t(3);
+    int u[kGather];
+    load_window_rw(lst, a, lo, hi, -1, u);
+    for (; a < hi; a += kWindow) {
+      int un[kGather];
+      const bool more = a + kWindow < hi;
+      if (more) load_window_rw(lst, a + kWindow, lo, hi, -1, un);
+      int tt[kGather];
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) tt[q] = u[q] >= 0 ? ld_keep(p.tent + u[q], pol) : 0;
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) hit |= (u[q] >= 0 && tt[q] == t);
+      if (__any_sync(FULL, hit)) break;
+      if (more) {
+#pragma unroll
+        for (int q = 0; q < kGather; ++q) u[q] = un[q];
+      }
+    }
+  }
+  hit = __any_sync(FULL, hit);
+  int finisher = 1, lose = hit;
+  if (nch > 1) {
+    if (lane == 0) {
+      if (hit) atomicOr(&p.flag[gslot], 1);
+      __threadfence();
+      finisher = atomicAdd(&p.done_d[gslot], 1) == nch - 1;
+      lose = 0;
+      if (finisher) {
+        __threadfence();
+        lose = atomicExch(&p.flag[gslot], 0) != 0;
+        p.done_d[gslot] = 0;
+      }
+    }
+    finisher = __shfl_sync(FULL, finisher, 0);
+    lose = __shfl_sync(FULL, lose, 0);
+  }
+  const bool push = finisher && lose && lane == 0;
+  if (filt_next)  // the next round reads the list just written
+    items_push(fstage, v, push ? max(1, num_chunks(L1.x + L1.y, p.chunk)) : 0, gslot,
+               p.fitems[nxt], &p.ctrl->ficnt[nxt]);
+  else  // hand-over: back to reading the row
+    items_push(lstage, v, push ? num_chunks(d, p.chunk) : 0, gslot, p.items[nxt],
+               &p.ctrl->icnt[nxt]);
+  if (finisher && lane == 0) {
+    p.flen[round & 1][gslot] = make_int2(0, 0);  // counts of the list of round r + 2
+    if (lose) {
+      acc.nbig += 1;
+      acc.dsum += (unsigned long long)d;
+    } else {
+      p.color[v] = t;
+      acc.maxc = max(acc.maxc, t);
+      if (p.fin) p.fin[v] = round;
+    }
+  }
+}
+
 // ------------------------------------------------------------ work walkers --
 //
 // Both walkers hand a warp its share of the work in a fixed stride and load
@@ -507,10 +764,13 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
 // working on the current one, so their latency overlaps the gathers.
 
 // Work items k = start, start + stride, ... < count: calls
-// f(v, chunk, gslot, nch, s, d) for every item whose node is active.
+// f(v, chunk, gslot, nch, s, d) for every item whose node is active. The
+// next item's share of its row is prefetched into L2 when its node's degree
+// is <= pf_max_deg (above it the node reads a filtered list, not the row).
 template <class F>
 __device__ __forceinline__ void for_items(const Params& p, const int4* items, int64_t count,
-                                          bool topo, int64_t start, int64_t stride, F f) {
+                                          bool topo, int64_t start, int64_t stride, int pf_max_deg,
+                                          F f) {
   if (start >= count) return;
   const int4 none = make_int4(0, 0, -1, 0);
   int4 A = ld_cg4(items + start);
@@ -526,7 +786,8 @@ __device__ __forceinline__ void for_items(const Params& p, const int4* items, in
     }
     const int4 C = k + 2 * stride < count ? ld_cg4(items + k + 2 * stride) : none;
     if (cA == 0) f(A.x, A.y, A.z, A.w, sA, eA - sA);
-    if (k + stride < count && cB == 0 && lane_id() == 0) {  // B's neighbours, into L2
+    if (k + stride < count && cB == 0 && eB - sB <= pf_max_deg &&
+        lane_id() == 0) {  // B's neighbours, into L2
       const int64_t lo = (int64_t)sB + (int64_t)B.y * p.chunk;
       prefetch_l2(p, lo, min((int64_t)eB, lo + p.chunk));
     }
@@ -589,9 +850,12 @@ struct RoundView {
   int mode;    // MODE_TOPO or MODE_DATA
   int nsmall;  // low-degree nodes in the worklist
   int nbig;    // high-degree nodes in the worklist
-  int icnt;    // their work items
-  int nistat;  // work items of every high-degree node
+  int icnt;    // work items of the worklist's high-degree nodes (not filtered)
+  int nistat;  // work items of every high-degree node (not filtered)
+  int ficnt;   // work items of the worklist's filtered nodes
   int maxc;    // largest committed colour at round start
+  int r0;      // first round of neighbour filtering (0: not started)
+  int filt;    // nodes of degree > filt_deg read filtered lists this round
   unsigned long long dsum;  // degree sum of the worklist
 };
 
@@ -603,9 +867,15 @@ __device__ __forceinline__ RoundView read_round(const Params& p, int r) {
   rv.nbig = ld_cg(&p.ctrl->cnt[rv.par][B_BIG]);
   rv.icnt = ld_cg(&p.ctrl->icnt[rv.par]);
   rv.nistat = ld_cg(&p.ctrl->nistat);
+  rv.ficnt = ld_cg(&p.ctrl->ficnt[rv.par]);
   rv.maxc = ld_cg(&p.ctrl->maxc);
   rv.dsum = __ldcg(&p.ctrl->dsum[rv.par]);
   rv.mode = MODE_DATA;
+  // filtering in round r >= r0 iff the colours committed before round r - 1
+  // fit the bitmap with room for round r - 1's (a round adds at most 1 to maxc)
+  rv.r0 = p.filt_r0 > 0 ? p.filt_r0 : ld_cg(&p.ctrl->handoff_round);
+  rv.filt = p.alist[0] != nullptr && rv.r0 > 0 && r >= rv.r0 &&
+            ld_cg(&p.ctrl->maxc_start[(r - 1) & 1]) <= kFiltMaxC;
   return rv;
 }
 
@@ -648,8 +918,10 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
 #pragma unroll
   for (int k = 0; k < 4; ++k) c->cnt[nxt][k] = 0;
   c->icnt[nxt] = 0;
+  c->ficnt[nxt] = 0;
   c->dsum[nxt] = 0;
   c->rounds = r;
+  c->maxc_start[r & 1] = rv.maxc;
   if (rv.mode == MODE_TOPO)
     c->rounds_topo += 1;
   else
@@ -672,69 +944,188 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
   __threadfence();
 }
 
+// The loops that involve filtered nodes are functions of their own (not
+// inlined), so the register budget of the other loops stays as it is
+// without them; they run once per phase. From round r0 on, filtered nodes
+// have work items of their own (fitems); in round r0 (built from the items
+// of the unfiltered rounds) and in topology sweeps (static items) they are
+// mixed with the others.
+
+// Assignment step of work items [k = gwarp, gwarp + nwarps, ...) of a list.
 template <int BS>
-__device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv, Team tm) {
-  const int warp = threadIdx.x >> 5, lane = lane_id();
+__device__ __forceinline__ void assign_items(const Params& p, Smem<BS>& sm, const int4* items,
+                                             int count, bool topo, int maxc, Team tm) {
+  const int warp = threadIdx.x >> 5;
+  const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
+  unsigned* wb = sm.wbits[warp];
+  for_items(p, items, count, topo, gwarp, nwarps, INT_MAX,
+            [&](int v, int c, int gslot, int nch, int s, int d) {
+              item_assign(p, wb, v, s, d, c, nch, gslot, maxc);
+            });
+}
+
+// Filtered or not, by degree (round r0 and topology sweeps while filtering).
+template <int BS>
+__device__ __noinline__ void assign_mixed(const Params& p, Smem<BS>& sm, const int4* items,
+                                          int count, const RoundView& rv, Team tm) {
+  const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   const bool topo = rv.mode == MODE_TOPO;
-  {  // high-degree work items: one warp each
-    const int4* items = topo ? p.istat : p.items[rv.par];
-    const int count = topo ? rv.nistat : rv.icnt;
-    unsigned* wb = sm.wbits[warp];
-    for_items(p, items, count, topo, gwarp, nwarps,
-              [&](int v, int c, int gslot, int nch, int s, int d) {
-                item_assign(p, wb, v, s, d, c, nch, gslot, rv.maxc);
-              });
-  }
-  {  // low-degree nodes: 32 per warp
-    unsigned* wm = sm.small_w[warp];
-    const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
-    for_small<false>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
-                     [&](int v, int s, int d, int) { small_assign(p, v, s, d, wm); });
-  }
-  (void)lane;
+  const int round = rv.round, r0 = rv.r0, maxc = rv.maxc;
+  unsigned* wb = sm.wbits[warp];
+  for_items(p, items, count, topo, gwarp, nwarps, round == r0 ? INT_MAX : p.filt_deg,
+            [&](int v, int c, int gslot, int nch, int s, int d) {
+              if (d > p.filt_deg) {
+                const int ne = filt_items(p, round, r0, gslot, d);
+                if (c < ne) item_assign_filtered(p, wb, v, s, d, c, ne, gslot, round, r0, maxc);
+              } else {
+                item_assign(p, wb, v, s, d, c, nch, gslot, maxc);
+              }
+            });
+}
+
+// The worklist's filtered nodes in a data-driven round after r0.
+template <int BS>
+__device__ __noinline__ void assign_fitems(const Params& p, Smem<BS>& sm, const RoundView& rv,
+                                           Team tm) {
+  const int warp = threadIdx.x >> 5;
+  const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
+  unsigned* wb = sm.wbits[warp];
+  const int round = rv.round, r0 = rv.r0, maxc = rv.maxc;
+  for_items(p, p.fitems[rv.par], rv.ficnt, false, gwarp, nwarps, -1,
+            [&](int v, int c, int gslot, int nch, int s, int d) {
+              item_assign_filtered(p, wb, v, s, d, c, nch, gslot, round, r0, maxc);
+            });
 }
 
 template <int BS>
-__device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv, PhaseAcc& acc,
-                             Team tm) {
-  const int warp = threadIdx.x >> 5, lane = lane_id();
+__device__ __forceinline__ void assign_small_nodes(const Params& p, Smem<BS>& sm,
+                                                   const RoundView& rv, Team tm) {
+  const int warp = threadIdx.x >> 5;
+  const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
+  const bool topo = rv.mode == MODE_TOPO;
+  unsigned* wm = sm.small_w[warp];
+  const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
+  for_small<false>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
+                   [&](int v, int s, int d, int) { small_assign(p, v, s, d, wm); });
+}
+
+template <int BS, bool FILT>
+__device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv, Team tm) {
+  const bool topo = rv.mode == MODE_TOPO;
+  const int4* items = topo ? p.istat : p.items[rv.par];
+  const int count = topo ? rv.nistat : rv.icnt;
+  if (FILT && rv.filt && (topo || rv.round == rv.r0)) {
+    assign_mixed<BS>(p, sm, items, count, rv, tm);
+  } else {
+    assign_items<BS>(p, sm, items, count, topo, rv.maxc, tm);
+    if (FILT && rv.filt) assign_fitems<BS>(p, sm, rv, tm);
+  }
+  assign_small_nodes<BS>(p, sm, rv, tm);
+}
+
+// Conflict step of work items of a list; pushes through `stage`.
+template <int BS>
+__device__ __forceinline__ PhaseAcc detect_items(const Params& p, ItemStage& stage,
+                                                 const int4* items, int count, bool topo,
+                                                 int round, int nxt, Team tm) {
+  const int warp = threadIdx.x >> 5;
+  const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
+  PhaseAcc acc;
+  for_items(p, items, count, topo, gwarp, nwarps, INT_MAX,
+            [&](int v, int cidx, int gslot, int nch, int s, int d) {
+              item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round);
+            });
+  return acc;
+}
+
+// The filtered path for the items of filtered nodes (all of them when
+// `mixed` is false), the other path for the rest.
+template <int BS>
+__device__ __noinline__ PhaseAcc detect_filtered(const Params& p, Smem<BS>& sm, ItemStage& stage,
+                                                 const int4* items, int count, bool mixed,
+                                                 const RoundView& rv, Team tm) {
+  const int warp = threadIdx.x >> 5;
+  const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
+  const bool topo = rv.mode == MODE_TOPO;
+  const int nxt = rv.par ^ 1, round = rv.round, r0 = rv.r0;
+  Ctrl* c = p.ctrl;
+  PhaseAcc acc;
+  // the next round filters iff this round's starting maxc leaves room
+  const bool filt_next = ld_cg(&c->maxc_start[round & 1]) <= kFiltMaxC;
+  ItemStage st = stage;
+  ItemStage fstage{sm.stage_t[warp], 0};
+  for_items(p, items, count, topo, gwarp, nwarps, -1,
+            [&](int v, int cidx, int gslot, int nch, int s, int d) {
+              if (!mixed || d > p.filt_deg) {
+                const int ne = mixed ? filt_items(p, round, r0, gslot, d) : nch;
+                if (cidx < ne)
+                  item_detect_filtered(p, st, fstage, v, s, d, cidx, ne, gslot, nxt, acc, round,
+                                       filt_next);
+              } else {
+                item_detect(p, st, v, s, d, cidx, nch, gslot, nxt, acc, round);
+              }
+            });
+  items_flush(fstage, p.fitems[nxt], &c->ficnt[nxt]);
+  stage = st;
+  return acc;
+}
+
+template <int BS>
+__device__ __forceinline__ PhaseAcc detect_small_nodes(const Params& p, Smem<BS>& sm,
+                                                       const RoundView& rv, Team tm) {
+  const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   const bool topo = rv.mode == MODE_TOPO;
   const int nxt = rv.par ^ 1;
   Ctrl* c = p.ctrl;
-  {
-    const int4* items = topo ? p.istat : p.items[rv.par];
-    const int count = topo ? rv.nistat : rv.icnt;
-    ItemStage stage{sm.stage_i[warp], 0};
-    for_items(p, items, count, topo, gwarp, nwarps,
-              [&](int v, int cidx, int gslot, int nch, int s, int d) {
-                item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, rv.round);
-              });
-    items_flush(stage, p.items[nxt], &c->icnt[nxt]);
-  }
-  {
-    unsigned* wm = sm.small_w[warp];
-    WarpStage sg{sm.stage_s[warp], 0};
-    const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
-    for_small<true>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
-                    [&](int v, int s, int d, int t) {
-                      const bool lose = small_lose(p, v, s, d, t, wm);
-                      stage_push(sg, kStageSmall, v >= 0 && lose, v, p.wl[nxt],
-                                 &c->cnt[nxt][B_SMALL]);
-                      if (v >= 0) {
-                        if (lose) {
-                          acc.dsum += (unsigned long long)d;
-                        } else {
-                          p.color[v] = t;
-                          acc.maxc = max(acc.maxc, t);
-                          if (p.fin) p.fin[v] = rv.round;
-                        }
+  PhaseAcc acc;
+  unsigned* wm = sm.small_w[warp];
+  WarpStage sg{sm.stage_s[warp], 0};
+  const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
+  for_small<true>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
+                  [&](int v, int s, int d, int t) {
+                    const bool lose = small_lose(p, v, s, d, t, wm);
+                    stage_push(sg, kStageSmall, v >= 0 && lose, v, p.wl[nxt],
+                               &c->cnt[nxt][B_SMALL]);
+                    if (v >= 0) {
+                      if (lose) {
+                        acc.dsum += (unsigned long long)d;
+                      } else {
+                        p.color[v] = t;
+                        acc.maxc = max(acc.maxc, t);
+                        if (p.fin) p.fin[v] = rv.round;
                       }
-                    });
-    stage_flush(sg, p.wl[nxt], &c->cnt[nxt][B_SMALL]);
+                    }
+                  });
+  stage_flush(sg, p.wl[nxt], &c->cnt[nxt][B_SMALL]);
+  return acc;
+}
+
+__device__ __forceinline__ void acc_merge(PhaseAcc& a, const PhaseAcc& b) {
+  a.maxc = max(a.maxc, b.maxc);
+  a.dsum += b.dsum;
+  a.nbig += b.nbig;
+}
+
+template <int BS, bool FILT>
+__device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv, PhaseAcc& acc,
+                             Team tm) {
+  const int warp = threadIdx.x >> 5;
+  const bool topo = rv.mode == MODE_TOPO;
+  const int nxt = rv.par ^ 1;
+  const int4* items = topo ? p.istat : p.items[rv.par];
+  const int count = topo ? rv.nistat : rv.icnt;
+  ItemStage stage{sm.stage_i[warp], 0};
+  if (FILT && rv.filt && (topo || rv.round == rv.r0)) {
+    acc_merge(acc, detect_filtered<BS>(p, sm, stage, items, count, true, rv, tm));
+  } else {
+    acc_merge(acc, detect_items<BS>(p, stage, items, count, topo, rv.round, nxt, tm));
+    if (FILT && rv.filt)
+      acc_merge(acc, detect_filtered<BS>(p, sm, stage, p.fitems[rv.par], rv.ficnt, false, rv, tm));
   }
-  (void)lane;
+  items_flush(stage, p.items[nxt], &p.ctrl->icnt[nxt]);
+  acc_merge(acc, detect_small_nodes<BS>(p, sm, rv, tm));
 }
 
 __device__ __forceinline__ void trace_round1(const Params& p, uint64_t t0) {
@@ -803,6 +1194,45 @@ __device__ void publish_result(const Params& p, Team tm) {
 // The whole round loop of one graph by a team of CTAs (the whole grid for the
 // single-graph kernel, a few CTAs or one CTA for a graph of a batch), the
 // rounds separated by the team's bounded barrier.
+// Rounds r_start, r_start + 1, ... of one graph by a team of CTAs, separated
+// by the team's bounded barrier, until the worklist is empty. Without FILT
+// the loop stops early at the hand-over round (handoff_now), which it
+// records for continue_graph.
+template <int BS, bool FILT>
+__device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) {
+  Ctrl* c = p.ctrl;
+  const bool lead = tm.cta == 0 && threadIdx.x == 0;
+  for (int r = r_start;; ++r) {
+    RoundView rv = read_round(p, r);
+    const int64_t total = (int64_t)rv.nsmall + rv.nbig;
+    if (total == 0) break;
+    if (r > p.max_rounds) {
+      if (lead) atomicCAS(&c->status, 0, IPGC_ERR_NO_CONVERGE);
+      break;
+    }
+    if (!FILT && handoff_now(p, r, total, rv.dsum, rv.maxc)) {
+      if (lead) c->handoff_round = r;
+      break;
+    }
+    rv.mode = decide_mode_block<BS>(p, rv, total, sm);
+    round_begin(p, rv, r, total, tm);
+    assign_phase<BS, FILT>(p, sm, rv, tm);
+    if (!team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+    if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_assign = gtime();
+    {
+      PhaseAcc acc;
+      detect_phase<BS, FILT>(p, sm, rv, acc, tm);
+      phase_commit<BS>(p, sm, acc, rv.par ^ 1);
+    }
+    if (!team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+    if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_detect = gtime();
+  }
+}
+
+// The whole colouring of one graph by a team of CTAs (the whole grid for the
+// single-graph kernel, a few CTAs or one CTA for a graph of a batch). With
+// neighbour filtering enabled it may stop at the hand-over round, and
+// continue_graph (a second launch) finishes it.
 template <int BS>
 __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   Ctrl* c = p.ctrl;
@@ -816,30 +1246,28 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   }
   if (team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) {
     if (lead) trace_round1(p, t0);
-    for (int r = 2;; ++r) {
-      RoundView rv = read_round(p, r);
-      const int64_t total = (int64_t)rv.nsmall + rv.nbig;
-      if (total == 0) break;
-      if (r > p.max_rounds) {
-        if (lead) atomicCAS(&c->status, 0, IPGC_ERR_NO_CONVERGE);
-        break;
-      }
-      rv.mode = decide_mode_block<BS>(p, rv, total, sm);
-      round_begin(p, rv, r, total, tm);
-      assign_phase<BS>(p, sm, rv, tm);
-      if (!team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) break;
-      if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_assign = gtime();
-      {
-        PhaseAcc acc;
-        detect_phase<BS>(p, sm, rv, acc, tm);
-        phase_commit<BS>(p, sm, acc, rv.par ^ 1);
-      }
-      if (!team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) break;
-      if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_detect = gtime();
-    }
+    run_rounds<BS, false>(p, sm, tm, 2);
   }
   if (lead) c->t_end = gtime();
   if (p.out_done) publish_result<BS>(p, tm);
+}
+
+// The rounds from the hand-over round r0 on, with neighbour filtering; does
+// nothing when color_graph finished the colouring itself.
+template <int BS>
+__device__ void continue_graph(const Params& p, Smem<BS>& sm, Team tm) {
+  Ctrl* c = p.ctrl;
+  const int r0 = ld_cg(&c->handoff_round);
+  if (r0 == 0) return;
+  const bool lead = tm.cta == 0 && threadIdx.x == 0;
+  // list counts of every merge-state slot start at zero
+  const int ng = ld_cg(&c->ngslot);
+  for (int i = tm.cta * BS + threadIdx.x; i < ng; i += tm.ncta * BS) {
+    p.flen[0][i] = make_int2(0, 0);
+    p.flen[1][i] = make_int2(0, 0);
+  }
+  if (team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) run_rounds<BS, true>(p, sm, tm, r0);
+  if (lead) c->t_end = gtime();
 }
 
 }  // namespace ipgc

@@ -105,7 +105,9 @@ class Options(ctypes.Structure):
         ("trace_cap", ctypes.c_int32),
         ("fault_inject", ctypes.c_int32),
         ("policy_margin", ctypes.c_float),
-        ("reserved2", ctypes.c_int32),
+        ("filter_degree", ctypes.c_int32),
+        ("filter_start", ctypes.c_float),
+        ("reserved3", ctypes.c_int32),
     ]
 
 
@@ -177,6 +179,8 @@ class ColorOptions:
     blocks_per_sm: int = 0
     fault_inject: int = 0
     policy_margin: float = 0.05
+    filter_degree: int = 0  # 0: library default; < 0: neighbour filtering off
+    filter_start: float = 0.0  # 0: library default
 
     def to_c(self, trace_ptr: int = 0, trace_cap: int = 0, fin_ptr: int = 0) -> Options:
         o = Options()
@@ -194,6 +198,8 @@ class ColorOptions:
         o.fin_round = fin_ptr or None
         o.fault_inject = self.fault_inject
         o.policy_margin = self.policy_margin
+        o.filter_degree = self.filter_degree
+        o.filter_start = self.filter_start
         return o
 
 

@@ -156,6 +156,41 @@ def test_bucket_thresholds(ctx, t1, chunk):
         assert_parity(ctx, rp, cl, ref, mode=mode, t1=t1, chunk=chunk)
 
 
+@pytest.mark.parametrize("fdeg,t1,chunk,start", [(-1, 0, 0, 0.0), (1, 1, 32, 1.0), (24, 24, 64, 0.05),
+                                                  (100, 8, 33, 0.2), (256, 24, 1024, 1.0),
+                                                  (2000, 24, 256, 1.0), (0, 63, 4096, 0.01),
+                                                  (0, 0, 0, 0.0)])
+def test_neighbour_filtering(ctx, fdeg, t1, chunk, start):
+    # filtered lists for none, some or all high-degree nodes, handed over in
+    # an early or a late round, with one or many work items per node, in
+    # every mode and driver: the colours never change
+    rp, cl = graphgen.rmat(14, 16, seed=21)
+    ref = oracle.color(rp, cl)
+    for mode, driver in MODES:
+        assert_parity(ctx, rp, cl, ref, mode=mode, driver=driver, filter_degree=fdeg, t1=t1,
+                      chunk=chunk, filter_start=start)
+
+
+def complete(n):
+    a, b = np.triu_indices(n, 1)
+    return graphgen.from_edges(n, a.astype(np.int32), b.astype(np.int32))
+
+
+@pytest.mark.parametrize("n", [2046, 2047, 2048, 2049, 2100])
+def test_filtering_hands_over_beyond_the_bitmap(ctx, n):
+    # K_n: colour(v) = v + 1 and n rounds. Past 2046 colours the filtered
+    # nodes' bitmap could not hold every colour, so they go back to reading
+    # their rows: the hand-over round must not change a colour
+    rp, cl = complete(n)
+    for mode, driver, chunk in (("data", "persistent", 0), ("topo", "persistent", 512),
+                                ("threshold", "hostloop", 256)):
+        got, st = gpu_color(ctx, rp, cl, mode=mode, driver=driver, chunk=chunk, filter_degree=64,
+                            filter_start=1.0)
+        assert st.error == 0
+        assert np.array_equal(got, np.arange(1, n + 1)), (mode, driver)
+        assert st.rounds == n and st.num_colors == n
+
+
 @pytest.mark.parametrize("frac", [0.0, 0.3, 0.6, 0.9, 1.0, 5.0])
 def test_threshold_fraction_invariance(ctx, frac):
     rp, cl = graphgen.rmat(14, 8, seed=12)
