@@ -7,9 +7,13 @@ persistent driver) of the RMAT scale-22, edge-factor-16 graph (a, b, c, d =
 second of device time (edges/s), inputs resident in HBM.
 
 Also reported:
-  roofline      algorithmic bytes of the colouring kernel / its average
-                launch time (CUDA events on the launch stream), against the
-                measured HBM copy peak;
+  roofline      algorithmic bytes of one colouring / its average duration
+                (CUDA events on the launch stream around the call, which is
+                two launches: the rounds before the hand-over to neighbour
+                filtering and the rounds from it on), against the measured
+                HBM copy peak; per-kernel bytes and device times from the
+                round trace; DRAM traffic from the committed ncu summary when
+                it was taken on the current kernel sources;
   e2e           the same metric through ipgc_color_host (host buffers, the
                 copies inside the timed region);
   cpu_baseline  the CPU oracle, single-threaded, on a bounded sample;
@@ -335,6 +339,78 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over all ranks (timing: the slowest rank sets the job's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed / the slowest rank's time."""
+    return units_per_rank * steps * world / (max_ms / 1e3)
+
+
+def kernel_sources_hash():
+    """sha256 over the CUDA sources and the public header (what the ncu
+    counters in profiles/ were taken on)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1912_01478_gb300", "csrc")
+    files = sorted(f for f in os.listdir(cs) if f.endswith((".cu", ".cuh", ".h")))
+    for f in files:
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    with open(os.path.join(ROOT, "include", "ipgc.h"), "rb") as fh:
+        h.update(b"ipgc.h\0" + fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per colouring of this workload from the ncu summary in
+    profiles/ (line 'traffic_bytes_per_step: B sources: H'), or None when the
+    summary was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "rmat_s22_dram_traffic.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_step:"):
+                    parts = line.split()
+                    b, h = int(parts[1]), parts[3]
+                    return b if h == kernel_sources_hash() else None
+    except (OSError, ValueError, IndexError):
+        return None
+    return None
+
+
+def round_bytes(rp, cl, fin, modes):
+    """Per-round algorithmic bytes (index r - 1 for round r); see algorithmic_bytes."""
+    n = rp.size - 1
+    deg = np.diff(rp).astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    nlow = np.bincount(src[cl < src], minlength=n).astype(np.int64)
+    R = int(fin.max())
+    cnt_fin = np.bincount(fin, minlength=R + 2).astype(np.int64)
+    deg_fin = np.bincount(fin, weights=deg, minlength=R + 2).astype(np.int64)
+    low_fin = np.bincount(fin, weights=nlow, minlength=R + 2).astype(np.int64)
+    A = np.cumsum(cnt_fin[::-1])[::-1]
+    D = np.cumsum(deg_fin[::-1])[::-1]
+    L = np.cumsum(low_fin[::-1])[::-1]
+    out = [4 * (n + 1) + 4 * int((deg > 0).sum()) + 8 * n + 4 * int(A[2] if R >= 2 else 0)]
+    for r in range(2, R + 1):
+        a, d, l, w = int(A[r]), int(D[r]), int(L[r]), int(cnt_fin[r])
+        x = a - w
+        sweep = 4 * n if modes[r - 1] == 1 else 4 * a
+        out.append(8 * a + 8 * d + 4 * a + 12 * a + 8 * l + 4 * w + 4 * x + 2 * sweep)
+    return out
+
+
 def algorithmic_bytes(rp, cl, fin, modes):
     """Bytes the method must move, summed over rounds:
     round 1 (implicit assignment): rowptr, the first neighbour of every
@@ -455,8 +531,33 @@ def main():
     fin = torch.zeros(n, dtype=torch.int32, device=dev)
     _, st = ctx.color(drp, dcl, colors, opts, stream=stream, trace=trace, fin_round=fin)
     tr = ipgc.read_trace(trace, st.rounds)
-    rounds, ncolors = st.rounds, st.num_colors
-    alg_bytes = algorithmic_bytes(rp, cl, fin.cpu().numpy(), tr["mode"].tolist())
+    rounds, ncolors, r0 = st.rounds, st.num_colors, st.filter_round
+    fin_h = fin.cpu().numpy()
+    alg_bytes = algorithmic_bytes(rp, cl, fin_h, tr["mode"].tolist())
+    # per kernel: rounds before the hand-over round r0 and from it on, their
+    # bytes and device times (%globaltimer of the trace)
+    rb = round_bytes(rp, cl, fin_h, tr["mode"].tolist())
+    t_round_end = tr["t_detect"].astype(np.int64)
+    split = r0 - 1 if r0 > 0 else rounds
+    per_kernel = [{
+        "kernel": "persistent_kernel<256>",
+        "rounds": [1, split],
+        "algorithmic_bytes": int(sum(rb[:split])),
+        "device_ms": float(t_round_end[split - 1] - tr["t_begin"][0]) / 1e6,
+    }]
+    if r0 > 0:
+        per_kernel.append({
+            "kernel": "persistent_filt_kernel<256>",
+            "rounds": [r0, rounds],
+            "algorithmic_bytes": int(sum(rb[split:])),
+            "device_ms": float(t_round_end[rounds - 1] - tr["t_begin"][split]) / 1e6,
+        })
+    for k in per_kernel:
+        k["algorithmic_gbs"] = k["algorithmic_bytes"] / max(k["device_ms"], 1e-9) / 1e6
+    if args.driver == "hostloop":  # round 1, two per later round, the finishing kernel
+        launches_per_step = 2 + 2 * (rounds - 1)
+    else:  # the persistent kernel, then the filtering kernel (returns at once without a hand-over)
+        launches_per_step = 2 if opts.filter_degree >= 0 else 1
     del trace, fin
 
     # warm-up, then K timed steps bracketed by barrier + synchronize
@@ -482,10 +583,8 @@ def main():
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
     st = ctx.last_stats()
     assert st.error == 0 and st.rounds == rounds and st.num_colors == ncolors
+    total_ms = max_over_ranks(total_ms, world)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
     # end to end through the host-buffer entry point: copies inside the region
@@ -496,12 +595,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         ctx.color_host(hrp, hcl, hout, opts, stream=stream)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    e2e_val = nnz / e2e_s * world
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = nnz / float(t.item()) * world
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
+    e2e_val = job_value(nnz, 1, world, e2e_s * 1e3)
 
     if rank != 0:
         dist.destroy_process_group()
@@ -516,9 +611,10 @@ def main():
         torch.cuda.empty_cache()
         serving_out = serving_leg(args, ctx, dev, stream)
     hbm, src = peaks()
+    traffic = measured_traffic()
     avg_launch_s = float(np.mean(per_launch_ms)) / 1e3
     achieved_gbs = alg_bytes / avg_launch_s / 1e9
-    value = nnz * args.steps * world / (total_ms / 1e3)
+    value = job_value(nnz, args.steps, world, total_ms)
     out = {
         "metric": METRIC,
         "value": value,
@@ -541,6 +637,8 @@ def main():
             "rounds_topo": int(st.rounds_topo),
             "rounds_data": int(st.rounds_data),
             "schedule": f"{args.mode} (H = 0.6 n), driver {args.driver}",
+            "neighbour_filtering": {"filter_degree": "default (1024)", "start": "default (|WL| <= n/32)",
+                                    "filter_round": int(r0)},
             "l2": "inputs larger than L2 (col 513 MB vs 129 MB L2); no flush",
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
@@ -550,11 +648,16 @@ def main():
             "peak": hbm,
             "unit": "GB/s",
             "frac": achieved_gbs / hbm,
-            "traffic": None,
+            "traffic": traffic,
             "peak_source": src,
-            "algorithmic_bytes_per_launch": int(alg_bytes),
-            "avg_launch_ms": avg_launch_s * 1e3,
-            "kernel": "persistent_kernel<256>",
+            "algorithmic_bytes_per_step": int(alg_bytes),
+            "avg_step_ms": avg_launch_s * 1e3,
+            "kernels": " + ".join(k["kernel"] for k in per_kernel),
+            "launches_per_step": launches_per_step,
+            "per_kernel": per_kernel,
+            "traffic_source": "profiles/rmat_s22_dram_traffic.md (ncu dram__bytes_read.sum + "
+                              "dram__bytes_write.sum, both kernels, one colouring)"
+                              if traffic is not None else "no ncu summary for these kernel sources",
         },
         "e2e": {
             "value": e2e_val,
@@ -562,7 +665,7 @@ def main():
             "h2d_bytes_per_step": int(4 * (n + 1) + 4 * nnz),
             "d2h_bytes_per_step": int(4 * n),
         },
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": clk.summary(),
         "cpu_baseline": ({k: v for k, v in cpu.items() if k != "seconds"} if cpu else None),
         "batched": batched_out,

@@ -85,7 +85,8 @@ typedef struct ipgc_stats {
   int64_t edges_processed; /* sum over rounds of the degrees of the active nodes */
   uint64_t ns;             /* device time of the colouring loop (%globaltimer) */
   int32_t error;           /* IPGC_OK or the error the device reported */
-  int32_t reserved;
+  int32_t filter_round;    /* first round with neighbour filtering (0: none; see
+                              ipgc_options.filter_degree); always 0 for batches */
 } ipgc_stats;
 
 /* One record per round, written to ipgc_options.trace when it is non-NULL. */
@@ -135,7 +136,7 @@ typedef struct ipgc_options {
                              only; used while every colour is <= 2047. */
   float filter_start;     /* filtering starts at the first round r >= 3 whose worklist has at
                              most filter_start * n nodes of mean degree above the filter
-                             degree; 0 = default 1/160 */
+                             degree; 0 = default 1/32 */
   int32_t reserved3;
 } ipgc_options;
 

@@ -90,13 +90,14 @@ int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
 //   high-degree nodes [2 parities + static][item_cap]; per-node state of
 //   nodes with several items or with filtering: bits [gcap][kGWords],
 //   done_a, done_d, flag [gcap]; with neighbour filtering, the filtered lists
-//   [2 parities][nnz], their counts (int2) [2 parities][gcap] and the work
-//   items of filtered nodes [2 parities][item_cap].
+//   [2 buffers][nnz], their counts (int2) [2 buffers][gcap], list state and
+//   finalised-entry counts [gcap] each (contiguous after the counts), and
+//   the work items of filtered nodes [2 parities][item_cap].
 // A node of degree > t1 has more than t1 entries, so at most nnz / (t1 + 1)
 // exist, with at most nnz / chunk + (their number) items; a node with several
 // items has more than `chunk` entries and a filtered one more than filt_deg.
 struct WsLayout {
-  size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, total;
+  size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, fst_bytes, total;
 };
 
 using ipgc::effective_chunk;
@@ -124,8 +125,10 @@ WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk, int filt_deg) {
   L.gint_bytes = align256((size_t)gcap * sizeof(int32_t));
   L.alist_bytes = filt ? align256((size_t)nnz * sizeof(int32_t)) : 0;
   L.flen_bytes = filt ? align256((size_t)gcap * sizeof(int2)) : 0;
+  L.fst_bytes = filt ? align256((size_t)gcap * sizeof(int32_t)) : 0;
   L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes +
-            2 * L.alist_bytes + 2 * L.flen_bytes + (filt ? 2 * L.items_bytes : 0);
+            2 * L.alist_bytes + 2 * L.flen_bytes + 2 * L.fst_bytes +
+            (filt ? 2 * L.items_bytes : 0);
   return L;
 }
 
@@ -200,6 +203,10 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
     w += L.flen_bytes;
     p.flen[1] = (int2*)w;
     w += L.flen_bytes;
+    p.fst = (int32_t*)w;
+    w += L.fst_bytes;
+    p.fdead = (int32_t*)w;
+    w += L.fst_bytes;
     p.fitems[0] = (int4*)w;
     w += L.items_bytes;
     p.fitems[1] = (int4*)w;
@@ -232,7 +239,7 @@ void stats_from_ctrl(const Ctrl& c, ipgc_stats* st) {
   st->edges_processed = (int64_t)c.edges;
   st->ns = c.t_end >= c.t_start ? c.t_end - c.t_start : 0;
   st->error = c.status;
-  st->reserved = 0;
+  st->filter_round = c.handoff_round;
 }
 
 int check_graph_args(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
@@ -288,9 +295,9 @@ int run_hostloop(ipgc_ctx* ctx, const Params& p0, int bs, int blocks, cudaStream
       if (std::fabs(pr - 0.5f) >= p.mlp_margin) mode = pr > 0.5f ? IPGC_MODE_TOPO : IPGC_MODE_DATA;
     }
     if (p.filt_r0 == 0 && ipgc::handoff_now(p, r, total, ctx->h_ctrl->dsum[par], ctx->h_ctrl->maxc)) {
-      // hand over to neighbour filtering: list counts start at zero
+      // hand over to neighbour filtering: list counts and states start at zero
       const WsLayout L = ws_layout(p.n, p.nnz, p.t1, p.chunk, p.filt_deg);
-      IPGC_CUDA(ctx, cudaMemsetAsync(p.flen[0], 0, 2 * L.flen_bytes, s));
+      IPGC_CUDA(ctx, cudaMemsetAsync(p.flen[0], 0, 2 * L.flen_bytes + 2 * L.fst_bytes, s));
       p.filt_r0 = r;
     }
     IPGC_CUDA(ctx, ipgc::launch_assign(p, bs, blocks, r, mode, s));

@@ -37,7 +37,7 @@ namespace ipgc {
 // ------------------------------------------------------- persistent kernel --
 
 template <int BS>
-__global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(Params p) {
+__global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(const __grid_constant__ Params p) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
   color_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(Params p
 // The rounds after the hand-over to neighbour filtering (enqueued right after
 // persistent_kernel; returns at once when no hand-over happened).
 template <int BS>
-__global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_filt_kernel(Params p) {
+__global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_filt_kernel(const __grid_constant__ Params p) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
   continue_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_filt_kernel(Par
 // ------------------------------------------------------ host-loop kernels --
 
 template <int BS>
-__global__ void __launch_bounds__(BS, min_blocks(BS)) round1_kernel(Params p) {
+__global__ void __launch_bounds__(BS, min_blocks(BS)) round1_kernel(const __grid_constant__ Params p) {
   __shared__ Smem<BS> sm;
   const uint64_t t0 = gtime();
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctrl->t_start = t0;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) round1_kernel(Params p) {
 }
 
 template <int BS, bool FILT>
-__global__ void __launch_bounds__(BS, min_blocks(BS)) assign_kernel(Params p, int r, int mode) {
+__global__ void __launch_bounds__(BS, min_blocks(BS)) assign_kernel(const __grid_constant__ Params p, int r, int mode) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
   // the previous round ended when this launch began
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) assign_kernel(Params p, in
 }
 
 template <int BS, bool FILT>
-__global__ void __launch_bounds__(BS, min_blocks(BS)) detect_kernel(Params p, int r, int mode) {
+__global__ void __launch_bounds__(BS, min_blocks(BS)) detect_kernel(const __grid_constant__ Params p, int r, int mode) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
   if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace && r <= p.trace_cap)

@@ -26,7 +26,7 @@ constexpr int kMaxChunk = 4096;
 constexpr int kGWords = 64;      // per-warp / per-node bitmap: colours 1..2048
 constexpr int kFiltMaxC = 32 * kGWords - 2;  // neighbour filtering while maxc <= this
 constexpr int kDefaultFiltDeg = 1024;
-constexpr double kDefaultFiltStart = 1.0 / 160;  // hand over once |WL| <= n / 160
+constexpr double kDefaultFiltStart = 1.0 / 32;  // hand over once |WL| <= n / 32
 constexpr int kStageSmall = 128; // per-warp staging of low-degree pushes
 constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
 
@@ -84,15 +84,19 @@ struct Params {
   float mlp_margin;   // learned policy: threshold rule when |p - 0.5| < margin
   // Neighbour filtering (alist[0] == nullptr: off). From the hand-over round
   // r0 on, a node of degree > filt_deg (>= chunk, so it has a merge-state
-  // slot) that is active in round r > r0 reads only the list of its
-  // neighbours still active in round r - 1, kept in alist[r & 1] inside the
-  // node's own row range [rowptr[v], rowptr[v + 1]): lower IDs from the front,
-  // higher IDs from the back, their counts in flen[r & 1][gslot]; in round r0
-  // it reads the row itself. Colours of its finalised neighbours accumulate in
-  // gbits[gslot] across rounds. Used in round r iff every colour committed
-  // before round r - 1 is <= kFiltMaxC, so the bitmap holds every colour.
+  // slot) reads a list that holds every neighbour still active (round r0: the
+  // row itself), kept in alist[b] inside the node's own row range
+  // [rowptr[v], rowptr[v + 1]): lower IDs from the front, higher IDs from the
+  // back, their counts in flen[b][gslot]; b = fst[gslot] & 1, and bit 1 of
+  // fst asks for a rewrite without finalised entries in the next round
+  // (fdead counts the finalised entries the last reading found). Colours of
+  // its finalised neighbours accumulate in gbits[gslot] across rounds. Used
+  // in round r iff every colour committed before round r - 1 is <=
+  // kFiltMaxC, so the bitmap holds every colour.
   int32_t* alist[2];
   int2* flen[2];
+  int32_t* fst;
+  int32_t* fdead;
   int4* fitems[2];    // work items of filtered nodes, per parity (as items[])
   int32_t filt_deg;
   int32_t filt_r0;    // host-loop driver: the hand-over round once reached (0: not yet)

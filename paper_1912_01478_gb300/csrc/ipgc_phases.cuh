@@ -526,48 +526,46 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
 // ------------------------------------------------------ neighbour filtering --
 //
 // Filtering starts at round r0 (the hand-over round, see continue_graph).
-// A filtered node v reads in round r the list of its neighbours that were
-// active in round r - 1 (in round r0: its whole row). A neighbour found
-// committed is finalised for good: its colour goes into v's persistent
-// bitmap and it leaves the list. The others are written to the list of round
-// r + 1, which is then exactly v's set of neighbours active in round r: the
-// only ones the conflict step can find a clash with (a finalised neighbour's
-// colour is excluded from tent[v]). The colours, rounds and worklists are
-// those of rescanning the whole row; only the entries read shrink.
+// A filtered node v keeps a list of neighbours that holds every neighbour
+// still active, in one of two buffers (state fst[gslot]: bit 0 the buffer,
+// bit 1 "rewrite in the next round"). In round r0 the list is built from the
+// row. Later rounds read the list: a neighbour found committed is finalised
+// for good, its colour goes into v's persistent bitmap. Most neighbours of a
+// long-lived high-degree node stay active from round to round, so the list
+// is rewritten (into the other buffer, without its finalised entries) only
+// once a quarter of it was found finalised; until then the finalised
+// entries are read again, harmlessly (their colours are in the bitmap
+// already and cannot clash: tent[v] excludes them). The conflict step scans
+// the lower-ID part of the list. Colours, rounds and worklists are those of
+// rescanning the whole row; only the entries read shrink.
 
 // Work items of filtered node v in round r: chunks of its list.
 __device__ __forceinline__ int filt_items(const Params& p, int round, int r0, int gslot, int d) {
   if (round == r0) return num_chunks(d, p.chunk);
-  const int2 L = __ldcg(p.flen[round & 1] + gslot);
+  const int cur = ld_cg(p.fst + gslot) & 1;
+  const int2 L = __ldcg(p.flen[cur] + gslot);
   return max(1, num_chunks(L.x + L.y, p.chunk));
 }
 
-// Entries [lo, hi) of v's current list (absolute indexes into src; src is
-// col in round r0): colours of committed neighbours into pm (1..32,
-// lane-private) and wb (33..2048); active neighbours appended to the next
-// list dst within v's row range [s, s + d), lower IDs from the front and
-// higher IDs from the back, counted in *nlen.
+// Entries [lo, hi) of v's list (absolute indexes into src; src is col in
+// round r0): colours of committed neighbours into pm (1..32, lane-private)
+// and wb (33..2048), their number added to dead. With `write`, active
+// neighbours are appended to the list dst within v's row range [s, s + d),
+// lower IDs from the front and higher IDs from the back, counted in *nlen.
 __device__ __forceinline__ void filt_assign_range(const Params& p, const int32_t* src, bool from_col,
                                                   int64_t lo, int64_t hi, int v, int64_t s, int d,
-                                                  int32_t* dst, int2* nlen, unsigned& pm,
-                                                  unsigned* wb) {
+                                                  bool write, int32_t* dst, int2* nlen,
+                                                  unsigned& pm, int& dead, unsigned* wb) {
+  // one window at a time: the lists are mostly in L2, and the registers a
+  // second window would take are worth more than the overlap
   const int lane = lane_id();
   const uint64_t pol = l2_keep_policy();
-  int64_t a = lo & ~int64_t(3);
-  int u[kGather];
-  if (from_col)
-    load_window(p, a, lo, hi, -1, u);
-  else
-    load_window_rw(src, a, lo, hi, -1, u);
-  for (; a < hi; a += kWindow) {
-    int un[kGather];
-    const bool more = a + kWindow < hi;
-    if (more) {
-      if (from_col)
-        load_window(p, a + kWindow, lo, hi, -1, un);
-      else
-        load_window_rw(src, a + kWindow, lo, hi, -1, un);
-    }
+  for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
+    int u[kGather];
+    if (from_col)
+      load_window(p, a, lo, hi, -1, u);
+    else
+      load_window_rw(src, a, lo, hi, -1, u);
     int cc[kGather];
 #pragma unroll
     for (int q = 0; q < kGather; ++q) cc[q] = u[q] >= 0 ? ld_keep(p.color + u[q], pol) : 0;
@@ -581,42 +579,39 @@ __device__ __forceinline__ void filt_assign_range(const Params& p, const int32_t
           ++klo;
         else
           ++khi;
-      } else if (c <= 32) {
-        pm |= 1u << (c - 1);
-      } else if (c <= 32 * kGWords) {
-        atomicOr(&wb[(c - 1) >> 5], 1u << ((c - 1) & 31));
+      } else {
+        ++dead;
+        if (c <= 32)
+          pm |= 1u << (c - 1);
+        else if (c <= 32 * kGWords)
+          atomicOr(&wb[(c - 1) >> 5], 1u << ((c - 1) & 31));
       }
     }
-    int xlo = klo, xhi = khi;  // inclusive prefix sums over the lanes
+    if (!write) continue;
+    // both counts in one prefix sum: a window holds at most 256 entries
+    int x = klo | (khi << 16);
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int ylo = __shfl_up_sync(FULL, xlo, o), yhi = __shfl_up_sync(FULL, xhi, o);
-      if (lane >= o) {
-        xlo += ylo;
-        xhi += yhi;
-      }
+      const int y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
     }
-    const int tlo = __shfl_sync(FULL, xlo, 31), thi = __shfl_sync(FULL, xhi, 31);
-    if (tlo | thi) {
-      int blo = 0, bhi = 0;
-      if (lane == 0) {
-        if (tlo) blo = atomicAdd(&nlen->x, tlo);
-        if (thi) bhi = atomicAdd(&nlen->y, thi);
-      }
-      int olo = __shfl_sync(FULL, blo, 0) + xlo - klo;
-      int ohi = __shfl_sync(FULL, bhi, 0) + xhi - khi;
-#pragma unroll
-      for (int q = 0; q < kGather; ++q) {
-        if (u[q] < 0 || cc[q] != 0) continue;
-        if (u[q] < v)
-          dst[s + olo++] = u[q];
-        else
-          dst[s + d - 1 - ohi++] = u[q];
-      }
+    const int tot = __shfl_sync(FULL, x, 31);
+    if (tot == 0) continue;
+    int blo = 0, bhi = 0;
+    if (lane == 0) {
+      if (tot & 0xffff) blo = atomicAdd(&nlen->x, tot & 0xffff);
+      if (tot >> 16) bhi = atomicAdd(&nlen->y, tot >> 16);
     }
-    if (more) {
+    const int xe = x - (klo | (khi << 16));  // exclusive prefix of this lane
+    int olo = __shfl_sync(FULL, blo, 0) + (xe & 0xffff);
+    int ohi = __shfl_sync(FULL, bhi, 0) + (xe >> 16);
 #pragma unroll
-      for (int q = 0; q < kGather; ++q) u[q] = un[q];
+    for (int q = 0; q < kGather; ++q) {
+      if (u[q] < 0 || cc[q] != 0) continue;
+      if (u[q] < v)
+        dst[s + olo++] = u[q];
+      else
+        dst[s + d - 1 - ohi++] = u[q];
     }
   }
 }
@@ -627,25 +622,31 @@ __device__ __forceinline__ void item_assign_filtered(const Params& p, unsigned* 
                                                      int d, int c, int nch, int gslot, int round,
                                                      int r0, int maxc) {
   const int lane = lane_id();
-  const int nb = (round + 1) & 1;
-  int32_t* dst = p.alist[nb];
-  int2* nlen = p.flen[nb] + gslot;
   unsigned pm = 0;
-  if (round == r0) {  // the first filtered round builds the list from the row
+  int dead = 0;
+  if (round == r0) {  // the first filtered round builds the list (buffer 0) from the row
     const int b = c * p.chunk, e = min(d, b + p.chunk);
-    filt_assign_range(p, p.col, true, (int64_t)s + b, (int64_t)s + e, v, s, d, dst, nlen, pm, wb);
+    filt_assign_range(p, p.col, true, (int64_t)s + b, (int64_t)s + e, v, s, d, true, p.alist[0],
+                      p.flen[0] + gslot, pm, dead, wb);
   } else {
-    // the list: [0, L.x) at s + k, [L.x, L.x + L.y) at s + d - L.y + (k - L.x)
-    const int32_t* src = p.alist[round & 1];
-    const int2 L = __ldcg(p.flen[round & 1] + gslot);
+    // the list in buffer cur: [0, L.x) at s + k, [L.x, L.x + L.y) at s + d - L.y + (k - L.x)
+    const int st = ld_cg(p.fst + gslot), cur = st & 1;
+    const bool rewrite = (st >> 1) & 1;
+    const int32_t* src = p.alist[cur];
+    int32_t* dst = p.alist[cur ^ 1];
+    int2* nlen = p.flen[cur ^ 1] + gslot;
+    const int2 L = __ldcg(p.flen[cur] + gslot);
     const int b = c * p.chunk, e = min(L.x + L.y, b + p.chunk);
     if (b < L.x)
-      filt_assign_range(p, src, false, (int64_t)s + b, (int64_t)s + min(e, L.x), v, s, d, dst,
-                        nlen, pm, wb);
+      filt_assign_range(p, src, false, (int64_t)s + b, (int64_t)s + min(e, L.x), v, s, d, rewrite,
+                        dst, nlen, pm, dead, wb);
     if (e > L.x) {
       const int64_t h0 = (int64_t)s + d - L.y - L.x;
-      filt_assign_range(p, src, false, h0 + max(b, L.x), h0 + e, v, s, d, dst, nlen, pm, wb);
+      filt_assign_range(p, src, false, h0 + max(b, L.x), h0 + e, v, s, d, rewrite, dst, nlen, pm,
+                        dead, wb);
     }
+    dead = __reduce_add_sync(FULL, dead);
+    if (!rewrite && dead && lane == 0) atomicAdd(p.fdead + gslot, dead);
   }
   pm = __reduce_or_sync(FULL, pm);
   __syncwarp();
@@ -684,41 +685,40 @@ __device__ __forceinline__ void item_assign_filtered(const Params& p, unsigned* 
 }
 
 // Conflict step for work item c of nch of filtered node v in round r: its
-// share of v's lower-ID active neighbours (the front part of the list the
-// assignment step wrote). The warp that finishes v's last item commits v or
-// pushes its items for round r + 1 (shaped for filtering when filt_next).
+// share of the lower-ID part of v's list as the assignment step left it. The
+// warp that finishes v's last item commits v or pushes its items for round
+// r + 1 (shaped for filtering when filt_next) and updates v's list state.
 __device__ __forceinline__ void item_detect_filtered(const Params& p, ItemStage& lstage,
                                                      ItemStage& fstage, int v, int s, int d, int c,
                                                      int nch, int gslot, int nxt, PhaseAcc& acc,
-                                                     int round, bool filt_next) {
+                                                     int round, int r0, bool filt_next) {
   const int lane = lane_id();
   const uint64_t pol = l2_keep_policy();
   const int t = ld_cg(p.tent + v);
-  const int nb = (round + 1) & 1;
+  // the list after this round's assignment step: buffer 0 in round r0, the
+  // other buffer after a rewrite, else the same one
+  int cur = 0, nb = 0;
+  bool rewrote = true;
+  if (round != r0) {
+    const int st = ld_cg(p.fst + gslot);
+    cur = st & 1;
+    rewrote = (st >> 1) & 1;
+    nb = rewrote ? cur ^ 1 : cur;
+  }
   const int2 L1 = __ldcg(p.flen[nb] + gslot);
   const int32_t* lst = p.alist[nb];
   const int64_t lo = (int64_t)s + (int64_t)L1.x * c / nch;
   const int64_t hi = (int64_t)s + (int64_t)L1.x * (c + 1) / nch;
   bool hit = false;
-  if (lo < hi) {
-    int64_t a = lo & ~int64_t(3);
+  for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
     int u[kGather];
     load_window_rw(lst, a, lo, hi, -1, u);
-    for (; a < hi; a += kWindow) {
-      int un[kGather];
-      const bool more = a + kWindow < hi;
-      if (more) load_window_rw(lst, a + kWindow, lo, hi, -1, un);
-      int tt[kGather];
+    int tt[kGather];
 #pragma unroll
-      for (int q = 0; q < kGather; ++q) tt[q] = u[q] >= 0 ? ld_keep(p.tent + u[q], pol) : 0;
+    for (int q = 0; q < kGather; ++q) tt[q] = u[q] >= 0 ? ld_keep(p.tent + u[q], pol) : 0;
 #pragma unroll
-      for (int q = 0; q < kGather; ++q) hit |= (u[q] >= 0 && tt[q] == t);
-      if (__any_sync(FULL, hit)) break;
-      if (more) {
-#pragma unroll
-        for (int q = 0; q < kGather; ++q) u[q] = un[q];
-      }
-    }
+    for (int q = 0; q < kGather; ++q) hit |= (u[q] >= 0 && tt[q] == t);
+    if (__any_sync(FULL, hit)) break;
   }
   hit = __any_sync(FULL, hit);
   int finisher = 1, lose = hit;
@@ -738,14 +738,19 @@ __device__ __forceinline__ void item_detect_filtered(const Params& p, ItemStage&
     lose = __shfl_sync(FULL, lose, 0);
   }
   const bool push = finisher && lose && lane == 0;
-  if (filt_next)  // the next round reads the list just written
+  if (filt_next)  // the next round reads the list
     items_push(fstage, v, push ? max(1, num_chunks(L1.x + L1.y, p.chunk)) : 0, gslot,
                p.fitems[nxt], &p.ctrl->ficnt[nxt]);
   else  // hand-over: back to reading the row
     items_push(lstage, v, push ? num_chunks(d, p.chunk) : 0, gslot, p.items[nxt],
                &p.ctrl->icnt[nxt]);
   if (finisher && lane == 0) {
-    p.flen[round & 1][gslot] = make_int2(0, 0);  // counts of the list of round r + 2
+    // list state for round r + 1: rewrite it once a quarter of it is finalised
+    const int dead = rewrote ? 0 : ld_cg(p.fdead + gslot);
+    const bool rw_next = 4 * (int64_t)dead >= (int64_t)(L1.x + L1.y) && dead > 0;
+    if (round != r0 && rewrote) p.flen[cur][gslot] = make_int2(0, 0);  // the old buffer is free
+    p.fst[gslot] = nb | (rw_next ? 2 : 0);
+    p.fdead[gslot] = 0;
     if (lose) {
       acc.nbig += 1;
       acc.dsum += (unsigned long long)d;
@@ -796,6 +801,18 @@ __device__ __forceinline__ void for_items(const Params& p, const int4* items, in
     eA = eB;
     cA = cB;
     B = C;
+  }
+}
+
+// The same without loading ahead (fewer registers), for the short item
+// lists of filtered nodes; every item's node is active (data-driven).
+template <class F>
+__device__ __forceinline__ void for_items_plain(const Params& p, const int4* items, int64_t count,
+                                                int64_t start, int64_t stride, F f) {
+  for (int64_t k = start; k < count; k += stride) {
+    const int4 A = ld_cg4(items + k);
+    const int sA = ld_ro(p.rowptr + A.x), eA = ld_ro(p.rowptr + A.x + 1);
+    f(A.x, A.y, A.z, A.w, sA, eA - sA);
   }
 }
 
@@ -992,10 +1009,10 @@ __device__ __noinline__ void assign_fitems(const Params& p, Smem<BS>& sm, const 
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   unsigned* wb = sm.wbits[warp];
   const int round = rv.round, r0 = rv.r0, maxc = rv.maxc;
-  for_items(p, p.fitems[rv.par], rv.ficnt, false, gwarp, nwarps, -1,
-            [&](int v, int c, int gslot, int nch, int s, int d) {
-              item_assign_filtered(p, wb, v, s, d, c, nch, gslot, round, r0, maxc);
-            });
+  for_items_plain(p, p.fitems[rv.par], rv.ficnt, gwarp, nwarps,
+                  [&](int v, int c, int gslot, int nch, int s, int d) {
+                    item_assign_filtered(p, wb, v, s, d, c, nch, gslot, round, r0, maxc);
+                  });
 }
 
 template <int BS>
@@ -1015,11 +1032,14 @@ __device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
   const bool topo = rv.mode == MODE_TOPO;
   const int4* items = topo ? p.istat : p.items[rv.par];
   const int count = topo ? rv.nistat : rv.icnt;
+  // (a call saves and restores registers in every thread, so warps without
+  // an item of a list skip it)
+  const int gwarp = tm.cta * (BS / 32) + (threadIdx.x >> 5);
   if (FILT && rv.filt && (topo || rv.round == rv.r0)) {
-    assign_mixed<BS>(p, sm, items, count, rv, tm);
+    if (gwarp < count) assign_mixed<BS>(p, sm, items, count, rv, tm);
   } else {
     assign_items<BS>(p, sm, items, count, topo, rv.maxc, tm);
-    if (FILT && rv.filt) assign_fitems<BS>(p, sm, rv, tm);
+    if (FILT && rv.filt && gwarp < rv.ficnt) assign_fitems<BS>(p, sm, rv, tm);
   }
   assign_small_nodes<BS>(p, sm, rv, tm);
 }
@@ -1039,12 +1059,12 @@ __device__ __forceinline__ PhaseAcc detect_items(const Params& p, ItemStage& sta
   return acc;
 }
 
-// The filtered path for the items of filtered nodes (all of them when
-// `mixed` is false), the other path for the rest.
+// Conflict step, filtered or not by degree (round r0 and topology sweeps
+// while filtering).
 template <int BS>
-__device__ __noinline__ PhaseAcc detect_filtered(const Params& p, Smem<BS>& sm, ItemStage& stage,
-                                                 const int4* items, int count, bool mixed,
-                                                 const RoundView& rv, Team tm) {
+__device__ __noinline__ PhaseAcc detect_mixed(const Params& p, Smem<BS>& sm, ItemStage& stage,
+                                              const int4* items, int count, const RoundView& rv,
+                                              Team tm) {
   const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   const bool topo = rv.mode == MODE_TOPO;
@@ -1057,15 +1077,38 @@ __device__ __noinline__ PhaseAcc detect_filtered(const Params& p, Smem<BS>& sm, 
   ItemStage fstage{sm.stage_t[warp], 0};
   for_items(p, items, count, topo, gwarp, nwarps, -1,
             [&](int v, int cidx, int gslot, int nch, int s, int d) {
-              if (!mixed || d > p.filt_deg) {
-                const int ne = mixed ? filt_items(p, round, r0, gslot, d) : nch;
+              if (d > p.filt_deg) {
+                const int ne = filt_items(p, round, r0, gslot, d);
                 if (cidx < ne)
                   item_detect_filtered(p, st, fstage, v, s, d, cidx, ne, gslot, nxt, acc, round,
-                                       filt_next);
+                                       r0, filt_next);
               } else {
                 item_detect(p, st, v, s, d, cidx, nch, gslot, nxt, acc, round);
               }
             });
+  items_flush(fstage, p.fitems[nxt], &c->ficnt[nxt]);
+  stage = st;
+  return acc;
+}
+
+// Conflict step of the worklist's filtered nodes in a data-driven round
+// after r0.
+template <int BS>
+__device__ __noinline__ PhaseAcc detect_fitems(const Params& p, Smem<BS>& sm, ItemStage& stage,
+                                               const RoundView& rv, Team tm) {
+  const int warp = threadIdx.x >> 5;
+  const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
+  const int nxt = rv.par ^ 1, round = rv.round, r0 = rv.r0;
+  Ctrl* c = p.ctrl;
+  PhaseAcc acc;
+  const bool filt_next = ld_cg(&c->maxc_start[round & 1]) <= kFiltMaxC;
+  ItemStage st = stage;
+  ItemStage fstage{sm.stage_t[warp], 0};
+  for_items_plain(p, p.fitems[rv.par], rv.ficnt, gwarp, nwarps,
+                  [&](int v, int cidx, int gslot, int nch, int s, int d) {
+                    item_detect_filtered(p, st, fstage, v, s, d, cidx, nch, gslot, nxt, acc,
+                                         round, r0, filt_next);
+                  });
   items_flush(fstage, p.fitems[nxt], &c->ficnt[nxt]);
   stage = st;
   return acc;
@@ -1117,12 +1160,13 @@ __device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
   const int4* items = topo ? p.istat : p.items[rv.par];
   const int count = topo ? rv.nistat : rv.icnt;
   ItemStage stage{sm.stage_i[warp], 0};
+  const int gwarp = tm.cta * (BS / 32) + warp;
   if (FILT && rv.filt && (topo || rv.round == rv.r0)) {
-    acc_merge(acc, detect_filtered<BS>(p, sm, stage, items, count, true, rv, tm));
+    if (gwarp < count) acc_merge(acc, detect_mixed<BS>(p, sm, stage, items, count, rv, tm));
   } else {
     acc_merge(acc, detect_items<BS>(p, stage, items, count, topo, rv.round, nxt, tm));
-    if (FILT && rv.filt)
-      acc_merge(acc, detect_filtered<BS>(p, sm, stage, p.fitems[rv.par], rv.ficnt, false, rv, tm));
+    if (FILT && rv.filt && gwarp < rv.ficnt)
+      acc_merge(acc, detect_fitems<BS>(p, sm, stage, rv, tm));
   }
   items_flush(stage, p.items[nxt], &p.ctrl->icnt[nxt]);
   acc_merge(acc, detect_small_nodes<BS>(p, sm, rv, tm));
@@ -1265,6 +1309,8 @@ __device__ void continue_graph(const Params& p, Smem<BS>& sm, Team tm) {
   for (int i = tm.cta * BS + threadIdx.x; i < ng; i += tm.ncta * BS) {
     p.flen[0][i] = make_int2(0, 0);
     p.flen[1][i] = make_int2(0, 0);
+    p.fst[i] = 0;
+    p.fdead[i] = 0;
   }
   if (team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) run_rounds<BS, true>(p, sm, tm, r0);
   if (lead) c->t_end = gtime();

@@ -47,11 +47,11 @@ class Stats(ctypes.Structure):
         ("edges_processed", ctypes.c_int64),
         ("ns", ctypes.c_uint64),
         ("error", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("filter_round", ctypes.c_int32),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class TraceRec(ctypes.Structure):
