@@ -229,6 +229,7 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.bar_extra = o.fault_inject ? 1u : 0u;
   p.mlp_margin = o.policy_margin;
   p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
+  p.shrink = o.driver == IPGC_DRIVER_PERSISTENT ? 1 : 0;
 }
 
 void stats_from_ctrl(const Ctrl& c, ipgc_stats* st) {

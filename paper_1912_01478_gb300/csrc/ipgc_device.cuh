@@ -19,7 +19,7 @@ constexpr unsigned FULL = 0xffffffffu;
 enum Bucket : int { B_SMALL = 0, B_BIG = 1, NB = 2 };
 
 constexpr int kMaxT1 = 63;       // 64-bit lane mask covers colours 1..64
-constexpr int kDefaultT1 = 24;
+constexpr int kDefaultT1 = 32;
 constexpr int kDefaultChunk = 1024;
 constexpr int kMinChunk = 32;
 constexpr int kMaxChunk = 4096;
@@ -27,6 +27,9 @@ constexpr int kGWords = 64;      // per-warp / per-node bitmap: colours 1..2048
 constexpr int kFiltMaxC = 32 * kGWords - 2;  // neighbour filtering while maxc <= this
 constexpr int kDefaultFiltDeg = 1024;
 constexpr double kDefaultFiltStart = 1.0 / 32;  // hand over once |WL| <= n / 32
+constexpr int kBarGroups = 16;   // grid barrier: CTAs arrive in this many groups
+constexpr int kBarFlat = 64;     // ... when the team has more CTAs than this
+constexpr int kShrinkMin = 8;    // a shrinking team keeps at least this many CTAs
 constexpr int kStageSmall = 128; // per-warp staging of low-degree pushes
 constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
 
@@ -50,6 +53,8 @@ struct Ctrl {
   int32_t ficnt[2];                // work items of the worklist's filtered nodes, per parity
   int32_t handoff_round;           // first round of neighbour filtering (0: none)
   int32_t pad[2];
+  // arrival counters of the grid barrier's groups, one 32-byte sector each
+  uint32_t bar_grp[kBarGroups][8];
 };
 
 struct Params {
@@ -100,6 +105,7 @@ struct Params {
   int4* fitems[2];    // work items of filtered nodes, per parity (as items[])
   int32_t filt_deg;
   int32_t filt_r0;    // host-loop driver: the hand-over round once reached (0: not yet)
+  int32_t shrink;     // the team may drop CTAs in small data-driven rounds (single graph)
   int64_t handoff_wl; // hand over when |WL| <= handoff_wl (0: never)
   // Optional result publication into host-mapped pinned memory (nullptr:
   // none). When a graph is done its team copies the colours to out_colors
@@ -223,8 +229,11 @@ struct Team {
 // residency), bounded by timeout_ns: a CTA that waits longer records
 // IPGC_ERR_TIMEOUT and leaves the barrier. Returns false when the team must
 // stop (timeout here or an error recorded elsewhere). The counters live in
-// the graph's control block. `extra` phantom CTAs never arrive (tests).
-__device__ __forceinline__ bool team_barrier(Ctrl* c, int ncta, uint64_t timeout_ns,
+// the graph's control block. A team of more than kBarFlat CTAs arrives in
+// kBarGroups groups (atomics on one counter serialise, so 16 short chains
+// and one of 16 beat one of hundreds). `extra` phantom CTAs never arrive
+// (tests).
+__device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_t timeout_ns,
                                              uint32_t extra = 0) {
   __shared__ int s_ok;
   __syncthreads();
@@ -232,8 +241,22 @@ __device__ __forceinline__ bool team_barrier(Ctrl* c, int ncta, uint64_t timeout
     volatile uint32_t* genp = &c->bar_gen;
     const uint32_t gen = *genp;
     __threadfence();
-    const uint32_t arrived = atomicAdd(&c->bar_count, 1u);
-    if (arrived == (uint32_t)ncta + extra - 1) {
+    bool last;
+    if (ncta > kBarFlat) {
+      // CTAs arrive on kBarGroups counters (CTA i in group i % kBarGroups);
+      // the last of a group resets its counter and arrives on the top one
+      const int g = cta % kBarGroups;
+      const uint32_t gsz = (uint32_t)(ncta / kBarGroups + (g < ncta % kBarGroups ? 1 : 0));
+      last = false;
+      if (atomicAdd(&c->bar_grp[g][0], 1u) == gsz - 1) {
+        c->bar_grp[g][0] = 0;
+        __threadfence();
+        last = atomicAdd(&c->bar_count, 1u) == (uint32_t)kBarGroups + extra - 1;
+      }
+    } else {
+      last = atomicAdd(&c->bar_count, 1u) == (uint32_t)ncta + extra - 1;
+    }
+    if (last) {
       c->bar_count = 0;
       __threadfence();
       atomicAdd(&c->bar_gen, 1u);
@@ -244,7 +267,7 @@ __device__ __forceinline__ bool team_barrier(Ctrl* c, int ncta, uint64_t timeout
           atomicCAS(&c->status, 0, IPGC_ERR_TIMEOUT);
           break;
         }
-        __nanosleep(32);
+        __nanosleep(64);
       }
     }
     __threadfence();

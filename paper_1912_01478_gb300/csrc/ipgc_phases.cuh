@@ -1259,16 +1259,29 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       break;
     }
     rv.mode = decide_mode_block<BS>(p, rv, total, sm);
+    if (p.shrink && rv.mode == MODE_DATA && tm.ncta > kShrinkMin) {
+      // a small round on a big team costs mostly barriers and idle passes:
+      // once a quarter of the team would do with one work unit (an item or
+      // 32 low-degree nodes) per warp, the CTAs beyond that leave for good
+      // (the worklist only shrinks)
+      const int64_t units = (int64_t)rv.icnt + (FILT ? rv.ficnt : 0) + ((int64_t)rv.nsmall + 31) / 32;
+      const int64_t want = (units + (BS / 32) - 1) / (BS / 32);
+      const int k = (int)(want > kShrinkMin ? want : kShrinkMin);
+      if (4 * k <= tm.ncta) {
+        if (tm.cta >= k) break;
+        tm.ncta = k;
+      }
+    }
     round_begin(p, rv, r, total, tm);
     assign_phase<BS, FILT>(p, sm, rv, tm);
-    if (!team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+    if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
     if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_assign = gtime();
     {
       PhaseAcc acc;
       detect_phase<BS, FILT>(p, sm, rv, acc, tm);
       phase_commit<BS>(p, sm, acc, rv.par ^ 1);
     }
-    if (!team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+    if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
     if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_detect = gtime();
   }
 }
@@ -1288,7 +1301,7 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
     round1<BS>(p, sm, acc, tm);
     phase_commit<BS>(p, sm, acc, 0);
   }
-  if (team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) {
+  if (team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) {
     if (lead) trace_round1(p, t0);
     run_rounds<BS, false>(p, sm, tm, 2);
   }
@@ -1312,7 +1325,7 @@ __device__ void continue_graph(const Params& p, Smem<BS>& sm, Team tm) {
     p.fst[i] = 0;
     p.fdead[i] = 0;
   }
-  if (team_barrier(c, tm.ncta, p.timeout_ns, p.bar_extra)) run_rounds<BS, true>(p, sm, tm, r0);
+  if (team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) run_rounds<BS, true>(p, sm, tm, r0);
   if (lead) c->t_end = gtime();
 }
 

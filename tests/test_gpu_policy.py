@@ -33,7 +33,8 @@ def test_features_from_trace(ctx):
     import torch
 
     tr = ipgc.trace_buffer(rp.size + 1)
-    _, st = ctx.color(torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda(), trace=tr)
+    _, st = ctx.color(torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda(), trace=tr,
+                      options=ipgc.ColorOptions(t1=24))
     rec = ipgc.read_trace(tr, st.rounds)
     f = policy.features(tr, st.rounds, rp.size - 1, cl.size).cpu().numpy()
     n, nnz = rp.size - 1, cl.size
