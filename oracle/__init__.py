@@ -56,6 +56,8 @@ def load_library(path: str):
     lib.oracle_color.restype = ctypes.c_int
     lib.oracle_push_iterations.argtypes = [i32, i32, P(i64), i64]
     lib.oracle_push_iterations.restype = i64
+    lib.oracle_push_run.argtypes = [i32, i32, i32, P(i64), P(i64), i64]
+    lib.oracle_push_run.restype = i64
     return lib
 
 
@@ -119,6 +121,22 @@ def color(rowptr, col, trace: bool = True, cap: int | None = None, lib=None) -> 
         wl[: min(r, cap)] if trace else None,
         ds[: min(r, cap)] if trace else None,
     )
+
+
+def push_run(n: int, count: int = 1000, mode: str = "wl"):
+    """Both Section III push kernels as written (mode "wl": Push_WL pops the
+    worklist; "nowl": Push_NoWL visits every node), run until the worklist is
+    empty. Returns (iterations, |WL| per iteration, sum of WL IDs per iteration)."""
+    lib = _load()
+    P = ctypes.POINTER(ctypes.c_int64)
+    cap = (n + count - 1) // count + 1 if count > 0 else 1
+    sizes = np.zeros(cap, np.int64)
+    sums = np.zeros(cap, np.int64)
+    it = lib.oracle_push_run(n, count, {"wl": 0, "nowl": 1}[mode], sizes.ctypes.data_as(P),
+                             sums.ctypes.data_as(P), cap)
+    if it < 0:
+        raise RuntimeError("oracle_push_run failed")
+    return int(it), sizes[:it], sums[:it]
 
 
 def push_iterations(n: int, count: int = 1000, cap: int = 0):

@@ -185,3 +185,57 @@ int64_t oracle_push_iterations(int32_t n, int32_t count, int64_t* sizes, int64_t
   }
   return iter;
 }
+
+/*
+ * Both kernels of the Section III micro-benchmark, run in a Pipe until the
+ * worklist is empty, as the paper writes them. mode 0 (Push_WL) pops every
+ * worklist entry and pushes it back iff it stays active; mode 1 (Push_NoWL)
+ * visits every node of the graph and pushes it iff it is active. A node v
+ * stays active in iteration i iff v >= count * (i + 1). After iteration i,
+ * sizes[i] = |WL| and sums[i] = the sum of the IDs in WL (optional arrays of
+ * cap entries). Returns the number of iterations.
+ */
+int64_t oracle_push_run(int32_t n, int32_t count, int32_t mode, int64_t* sizes, int64_t* sums,
+                        int64_t cap) {
+  if (n < 0 || count <= 0 || (mode != 0 && mode != 1)) return ORACLE_ERR_ARG;
+  int32_t* wl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* next = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (!wl || !next) {
+    free(wl);
+    free(next);
+    return ORACLE_ERR_OOM;
+  }
+  int64_t len = n;  /* WL = graph.nodes */
+  for (int32_t v = 0; v < n; ++v) wl[v] = v;
+  int64_t iter = 0;
+  while (len > 0) {
+    const int64_t thr = (int64_t)count * (iter + 1);
+    int64_t nlen = 0, sum = 0;
+    if (mode == 0) {
+      for (int64_t k = 0; k < len; ++k) {
+        const int32_t v = wl[k]; /* pop */
+        if (v >= thr) {
+          next[nlen++] = v; /* push */
+          sum += v;
+        }
+      }
+    } else {
+      for (int32_t v = 0; v < n; ++v) {
+        if (v >= thr) {
+          next[nlen++] = v;
+          sum += v;
+        }
+      }
+    }
+    if (sizes && iter < cap) sizes[iter] = nlen;
+    if (sums && iter < cap) sums[iter] = sum;
+    int32_t* t = wl;
+    wl = next;
+    next = t;
+    len = nlen;
+    ++iter;
+  }
+  free(wl);
+  free(next);
+  return iter;
+}

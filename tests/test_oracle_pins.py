@@ -272,3 +272,27 @@ def test_micro_benchmark_iterations():
         assert it == -(-n // count)
         k = min(it, 64)
         assert sizes[:k].tolist() == [max(n - count * (i + 1), 0) for i in range(k)]
+
+
+@pytest.mark.parametrize("mode", ["wl", "nowl"])
+def test_push_kernels_closed_form(mode):
+    # Section III: both kernels deactivate the same COUNT IDs per iteration, so
+    # after iteration i the worklist is {COUNT*(i+1), ..., n-1}: its size and
+    # the sum of its IDs are closed forms (a slip such as the listing's strict
+    # comparison keeps one extra node per iteration and fails here)
+    for n, count in [(0, 1000), (1, 1000), (999, 1000), (1000, 1000), (1001, 1000),
+                     (25_000, 1000), (10_007, 7), (5, 1)]:
+        it, sizes, sums = oracle.push_run(n, count, mode)
+        assert it == -(-n // count)
+        for i in range(it):
+            a = count * (i + 1)
+            m = max(n - a, 0)
+            assert sizes[i] == m
+            assert sums[i] == (m * (a + n - 1) // 2 if m else 0)
+
+
+def test_push_kernels_agree():
+    # the data-driven and topology-driven kernels do the same work (Section III)
+    a = oracle.push_run(12_345, 100, "wl")
+    b = oracle.push_run(12_345, 100, "nowl")
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
