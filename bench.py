@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000",
                     help="request rates of the serving leg (empty = skip)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--micro-n", type=int, default=50_912_018,
+                    help="nodes of the Section III micro-benchmark leg (0 = skip)")
     return ap.parse_args()
 
 
@@ -168,6 +170,42 @@ def serving_leg(args, ctx, dev, stream):
         "seconds_per_rate": args.serve_seconds,
         "rates": out_rates,
     }
+
+
+def micro_leg(args, ctx):
+    """Section III micro-benchmark at the europe_osm size (n = 50,912,018,
+    COUNT = 1000, 50,913 iterations in one launch): per-iteration time (TTI)
+    of Push_NoWL (topology-driven) and Push_WL (data-driven), their crossover
+    (first window of 500 iterations where Push_WL is faster on average), and
+    the hybrid switching at the worklist size of the crossover. Bytes moved:
+    Push_NoWL writes 4 |WL_next|; Push_WL reads 4 |WL| and writes 4 |WL_next|."""
+    n, count = args.micro_n, 1000
+    if n <= 0:
+        return None
+    out = {"workload": f"n = {n} (europe_osm's node count), COUNT = {count}", "n": n}
+    tti = {}
+    for mode in ("nowl", "wl"):
+        ctx.push_bench(n, count, mode)  # warm-up
+        it, rec = ctx.push_bench(n, count, mode)
+        t = rec[:, 3].astype(np.float64)
+        sizes = rec[:, 0].astype(np.float64)
+        before = np.concatenate([[n], sizes[:-1]])
+        moved = 4 * sizes.sum() + (4 * before.sum() if mode == "wl" else 0.0)
+        tti[mode] = t
+        out[mode] = {"iterations": int(it), "total_ms": t.sum() / 1e6,
+                     "tti_us_first100": t[:100].mean() / 1e3, "tti_us_last100": t[-100:].mean() / 1e3,
+                     "bytes_moved": moved, "gbs": moved / t.sum()}
+    d = tti["wl"] - tti["nowl"]
+    w = 500
+    cs = np.convolve(d, np.ones(w) / w, mode="valid")
+    x = int(np.argmax(cs < 0)) if (cs < 0).any() else len(d)
+    switch = max(n - count * (x + 1), 0)
+    it, rec = ctx.push_bench(n, count, "hybrid", switch)
+    out["crossover_iteration"] = x
+    out["crossover_wl"] = switch
+    out["hybrid"] = {"switch_wl": switch, "total_ms": rec[:, 3].sum() / 1e6}
+    out["per_iteration_best_ms"] = float(np.minimum(tti["wl"], tti["nowl"]).sum() / 1e6)
+    return out
 
 
 def batched_leg(args, ctx, dev, stream):
@@ -356,15 +394,19 @@ def job_value(units_per_rank: float, steps: int, world: int, max_ms: float) -> f
     return units_per_rank * steps * world / (max_ms / 1e3)
 
 
+COLOURING_SOURCES = ("ipgc_api.cu", "ipgc_color.cu", "ipgc_device.cuh", "ipgc_internal.h",
+                     "ipgc_phases.cuh")
+
+
 def kernel_sources_hash():
-    """sha256 over the CUDA sources and the public header (what the ncu
-    counters in profiles/ were taken on)."""
+    """sha256 over the sources the single-graph colouring kernels are built
+    from and the public header (what the ncu counters in profiles/ were
+    taken on)."""
     import hashlib
 
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1912_01478_gb300", "csrc")
-    files = sorted(f for f in os.listdir(cs) if f.endswith((".cu", ".cuh", ".h")))
-    for f in files:
+    for f in COLOURING_SOURCES:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     with open(os.path.join(ROOT, "include", "ipgc.h"), "rb") as fh:
@@ -606,6 +648,10 @@ def main():
         del drp, dcl, colors
         torch.cuda.empty_cache()
         batched_out = batched_leg(args, ctx, dev, stream)
+    micro_out = None
+    if world == 1 and args.micro_n > 0:
+        torch.cuda.empty_cache()
+        micro_out = micro_leg(args, ctx)
     serving_out = None
     if world == 1 and args.serve_rates:
         torch.cuda.empty_cache()
@@ -670,6 +716,7 @@ def main():
         "cpu_baseline": ({k: v for k, v in cpu.items() if k != "seconds"} if cpu else None),
         "batched": batched_out,
         "serving": serving_out,
+        "micro_benchmark": micro_out,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

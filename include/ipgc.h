@@ -404,6 +404,33 @@ IPGC_API int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int6
                                    float* best_ms, void* stream);
 
 /*
+ * The micro-benchmark of Section III (Listings "Push Kernels" and "Kernel
+ * Calls"): the worklist starts as all n nodes and iteration i deactivates
+ * the next `count` IDs (node v stays active iff v >= count * (i + 1), the
+ * text's reading of the listing), until the worklist is empty, i.e. for
+ * ceil(n / count) iterations. Each iteration keeps a worklist:
+ *   IPGC_PUSH_WL      Push_WL: iterate over the worklist (data-driven);
+ *   IPGC_PUSH_NOWL    Push_NoWL: iterate over all n nodes (topology-driven);
+ *   IPGC_PUSH_HYBRID  Push_NoWL while |WL| > switch_wl, then Push_WL.
+ * All iterations run in one cooperative launch (the Pipe). Arguments:
+ *   n          0 <= n < 2^31 nodes; count >= 1
+ *   rec        device pointer to cap records of 4 int64 each, or NULL (cap 0):
+ *              record i = {|WL| after iteration i, sum of the IDs in it, the
+ *              kernel used (IPGC_PUSH_WL / IPGC_PUSH_NOWL), the iteration's
+ *              time in ns (%globaltimer)}; iterations >= cap are not recorded
+ *   iterations host pointer (may be NULL): the number of iterations
+ * The worklists (2n int32) live in the context's auxiliary buffer. The call
+ * synchronises `stream`. Returns IPGC_OK, IPGC_ERR_INVALID, IPGC_ERR_OOM,
+ * IPGC_ERR_CUDA or IPGC_ERR_TIMEOUT (a bounded barrier gave up).
+ */
+#define IPGC_PUSH_WL 0
+#define IPGC_PUSH_NOWL 1
+#define IPGC_PUSH_HYBRID 2
+IPGC_API int ipgc_push_bench(ipgc_ctx* ctx, int64_t n, int32_t count, int32_t mode,
+                             int64_t switch_wl, int64_t* rec, int64_t cap, int64_t* iterations,
+                             void* stream);
+
+/*
  * Colour one graph without allocating anything (the paper has no counterpart;
  * this exists for callers that cannot allocate device memory when they need
  * a colouring, e.g. code running inside an allocator or memory-pool callback,

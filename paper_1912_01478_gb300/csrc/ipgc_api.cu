@@ -26,6 +26,9 @@ struct ipgc_ctx {
   int32_t* d_col = nullptr;
   int32_t* d_colors = nullptr;
   size_t cap_rowptr = 0, cap_col = 0, cap_colors = 0;
+  // auxiliary device buffer (micro-benchmark worklists), grown on demand
+  char* aux = nullptr;
+  size_t aux_bytes = 0;
   // learned policy weights
   float* d_mlp = nullptr;
   int32_t mlp_len = 0;
@@ -54,6 +57,24 @@ int ctx_device(const ipgc_ctx* ctx) { return ctx->device; }
 int ctx_num_sms(const ipgc_ctx* ctx) { return ctx->num_sms; }
 void ctx_note_cuda_error(ipgc_ctx* ctx, int err) { ctx->last_cuda = err; }
 const float* ctx_policy_weights(const ipgc_ctx* ctx) { return ctx->mlp_len ? ctx->d_mlp : nullptr; }
+Ctrl* ctx_ctrl_dev(ipgc_ctx* ctx) { return ctx->d_ctrl; }
+Ctrl* ctx_ctrl_host(ipgc_ctx* ctx) { return ctx->h_ctrl; }
+
+void* ctx_aux(ipgc_ctx* ctx, size_t bytes, int* rc) {
+  *rc = IPGC_OK;
+  if (ctx->aux && ctx->aux_bytes >= bytes) return ctx->aux;
+  if (ctx->aux) cudaFree(ctx->aux);
+  ctx->aux = nullptr;
+  ctx->aux_bytes = 0;
+  const cudaError_t e = cudaMalloc((void**)&ctx->aux, bytes ? bytes : 1);
+  if (e != cudaSuccess) {
+    ctx->last_cuda = (int)e;
+    *rc = e == cudaErrorMemoryAllocation ? IPGC_ERR_OOM : IPGC_ERR_CUDA;
+    return nullptr;
+  }
+  ctx->aux_bytes = bytes;
+  return ctx->aux;
+}
 
 }  // namespace ipgc
 
@@ -394,6 +415,7 @@ int ipgc_ctx_destroy(ipgc_ctx* ctx) {
     if (ctx->d_col) cudaFree(ctx->d_col);
     if (ctx->d_colors) cudaFree(ctx->d_colors);
     if (ctx->d_mlp) cudaFree(ctx->d_mlp);
+    if (ctx->aux) cudaFree(ctx->aux);
     ipgc::batched_release(ctx);
   }
   delete ctx;

@@ -212,6 +212,9 @@ __device__ __forceinline__ int32_t ld_keep(const int32_t* p, uint64_t pol) {
   return v;
 }
 __device__ __forceinline__ int4 ld_cg4(const int4* p) { return __ldcg(p); }
+__device__ __forceinline__ int64_t ld_cg_i64(const int64_t* p) {
+  return (int64_t)__ldcg(reinterpret_cast<const long long*>(p));
+}
 // Loads of the read-only graph.
 __device__ __forceinline__ int32_t ld_ro(const int32_t* p) { return __ldg(p); }
 

@@ -59,6 +59,11 @@ int ctx_device(const ipgc_ctx* ctx);
 int ctx_num_sms(const ipgc_ctx* ctx);
 void ctx_note_cuda_error(ipgc_ctx* ctx, int err);
 const float* ctx_policy_weights(const ipgc_ctx* ctx);
+Ctrl* ctx_ctrl_dev(ipgc_ctx* ctx);
+Ctrl* ctx_ctrl_host(ipgc_ctx* ctx);  // pinned
+// The context's auxiliary device buffer of at least `bytes` (grown on demand);
+// nullptr with *rc = IPGC_ERR_OOM / IPGC_ERR_CUDA on failure.
+void* ctx_aux(ipgc_ctx* ctx, size_t bytes, int* rc);
 int effective_t1(const ipgc_options& o);
 int effective_chunk(const ipgc_options& o);
 

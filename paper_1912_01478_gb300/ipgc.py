@@ -34,6 +34,7 @@ NOALLOC_MAX_NNZ = 8388608
 
 MODE_THRESHOLD, MODE_TOPO, MODE_DATA, MODE_LEARNED = 0, 1, 2, 3
 DRIVER_PERSISTENT, DRIVER_HOSTLOOP = 0, 1
+PUSH_WL, PUSH_NOWL, PUSH_HYBRID = 0, 1, 2
 MODES = {"threshold": MODE_THRESHOLD, "topo": MODE_TOPO, "data": MODE_DATA, "learned": MODE_LEARNED}
 DRIVERS = {"persistent": DRIVER_PERSISTENT, "hostloop": DRIVER_HOSTLOOP}
 
@@ -140,6 +141,7 @@ SIGNATURES = {
         [_P, _P, _P, _I32, _I64, _P, ctypes.POINTER(Stats), ctypes.POINTER(Options), _P],
     ),
     "ipgc_validate_csr": (_INT, [_P, _P, _P, _I32, _I64, _INT, _P]),
+    "ipgc_push_bench": (_INT, [_P, _I64, _I32, _I32, _I64, _P, _I64, ctypes.POINTER(_I64), _P]),
     "ipgc_color_noalloc": (_INT, [_P, _P, _I32, _I64, _P, ctypes.POINTER(Stats), _P]),
     "ipgc_autotune": (
         _INT,
@@ -302,6 +304,24 @@ class Context:
         )
         _check(rc, "ipgc_color_host")
         return colors_out, st
+
+    def push_bench(self, n: int, count: int = 1000, mode: str = "wl", switch_wl: int = 0,
+                   record: bool = True, stream=None):
+        """The Section III micro-benchmark (mode "wl", "nowl" or "hybrid").
+        Returns (iterations, records): records is a numpy int64 [iterations, 4]
+        array of (|WL| after, sum of its IDs, kernel used, time ns) or None."""
+        import torch
+
+        cap = (n + count - 1) // count if record and count > 0 else 0
+        rec = torch.zeros(max(cap, 1) * 4, dtype=torch.int64, device=f"cuda:{self.device}")
+        it = _I64(0)
+        m = {"wl": PUSH_WL, "nowl": PUSH_NOWL, "hybrid": PUSH_HYBRID}[mode]
+        rc = lib().ipgc_push_bench(self.handle, n, count, m, switch_wl,
+                                   rec.data_ptr() if cap else None, cap, ctypes.byref(it),
+                                   _stream_handle(stream) or None)
+        _check(rc, "ipgc_push_bench")
+        out = rec[: it.value * 4].view(-1, 4).cpu().numpy() if cap else None
+        return it.value, out
 
     def validate(self, rowptr, col, stream=None) -> int:
         """IPGC_OK or IPGC_ERR_INVALID for a CSR held in CUDA tensors."""
