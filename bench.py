@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000",
                     help="request rates of the serving leg (empty = skip)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--worklist-leg", type=int, default=1,
+                    help="compare the kept and the rebuilt worklist (0 = skip)")
     ap.add_argument("--micro-n", type=int, default=50_912_018,
                     help="nodes of the Section III micro-benchmark leg (0 = skip)")
     return ap.parse_args()
@@ -170,6 +172,41 @@ def serving_leg(args, ctx, dev, stream):
         "seconds_per_rate": args.serve_seconds,
         "rates": out_rates,
     }
+
+
+def worklist_leg(args, ctx, drp, dcl, stream):
+    """The paper's hybrid (the worklist kept in every round) against the
+    discard-and-rebuild hybrid (topology-driven rounds keep no worklist; it
+    is rebuilt on the way back), both without neighbour filtering, on the
+    headline graph at three thresholds H = frac * n; best of 3 colourings
+    each (CUDA events)."""
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc
+
+    if not args.worklist_leg:
+        return None
+    nnz = dcl.numel()
+    out = []
+    for frac in (0.6, 0.2, 0.05):
+        row = {"threshold_frac": frac}
+        for wl in ("keep", "rebuild"):
+            o = ipgc.ColorOptions(validate=False, filter_degree=-1, worklist=wl, threshold_frac=frac)
+            ctx.color(drp, dcl, options=o, stream=stream)
+            ts = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.color(drp, dcl, options=o, stream=stream, wait=False)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            st = ctx.last_stats()
+            row[wl] = {"ms": min(ts), "edges_per_s": nnz / (min(ts) / 1e3),
+                       "rounds_topo": int(st.rounds_topo), "rounds_data": int(st.rounds_data)}
+        row["rebuild_over_keep"] = row["rebuild"]["ms"] / row["keep"]["ms"]
+        out.append(row)
+    return {"workload": "the headline RMAT scale-22 graph", "filter": "off for both", "rows": out}
 
 
 def micro_leg(args, ctx):
@@ -643,6 +680,7 @@ def main():
     if rank != 0:
         dist.destroy_process_group()
         return
+    worklist_out = worklist_leg(args, ctx, drp, dcl, stream) if world == 1 else None
     batched_out = None
     if world == 1 and args.batch_graphs > 0:
         del drp, dcl, colors
@@ -717,6 +755,7 @@ def main():
         "batched": batched_out,
         "serving": serving_out,
         "micro_benchmark": micro_out,
+        "worklist_policy": worklist_out,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

@@ -137,8 +137,18 @@ typedef struct ipgc_options {
   float filter_start;     /* filtering starts at the first round r >= 3 whose worklist has at
                              most filter_start * n nodes of mean degree above the filter
                              degree; 0 = default 1/32 */
-  int32_t reserved3;
+  int32_t worklist;       /* IPGC_WORKLIST_KEEP (default): every round pushes the worklist,
+                             topology-driven ones too (the paper's hybrid, Sections I and IV);
+                             IPGC_WORKLIST_REBUILD: topology-driven rounds only count the
+                             active nodes and the first data-driven round after them rebuilds
+                             the worklist from the colours (the hybrid of Nasre et al. that the
+                             paper compares against, Section I). Same colours either way.
+                             REBUILD runs without neighbour filtering and only with the
+                             persistent driver (IPGC_ERR_UNSUPPORTED otherwise). */
 } ipgc_options;
+
+#define IPGC_WORKLIST_KEEP 0
+#define IPGC_WORKLIST_REBUILD 1
 
 /* Fill *opt with the defaults listed above. */
 IPGC_API void ipgc_options_default(ipgc_options* opt);

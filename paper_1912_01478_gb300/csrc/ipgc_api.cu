@@ -127,7 +127,7 @@ using ipgc::effective_t1;
 // Degree above which a node is filtered (INT32_MAX: off); at least the
 // chunk, so every such node has several work items and a merge-state slot.
 int effective_filt_deg(const ipgc_options& o) {
-  if (o.filter_degree < 0) return INT32_MAX;
+  if (o.filter_degree < 0 || o.worklist == IPGC_WORKLIST_REBUILD) return INT32_MAX;
   const int f = o.filter_degree > 0 ? o.filter_degree : ipgc::kDefaultFiltDeg;
   const int lo = effective_chunk(o) > effective_t1(o) ? effective_chunk(o) : effective_t1(o);
   return f > lo ? f : lo;
@@ -251,6 +251,7 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.mlp_margin = o.policy_margin;
   p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
   p.shrink = o.driver == IPGC_DRIVER_PERSISTENT ? 1 : 0;
+  p.wl_rebuild = o.worklist == IPGC_WORKLIST_REBUILD ? 1 : 0;
 }
 
 void stats_from_ctrl(const Ctrl& c, ipgc_stats* st) {
@@ -458,6 +459,9 @@ int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int3
   if (o.block_size != 0 && o.block_size != 256 && o.block_size != 512) return IPGC_ERR_UNSUPPORTED;
   if (o.trace && o.trace_cap < 0) return IPGC_ERR_INVALID;
   if (!(o.threshold_frac >= 0.0f)) return IPGC_ERR_INVALID;
+  if (o.worklist != IPGC_WORKLIST_KEEP && o.worklist != IPGC_WORKLIST_REBUILD) return IPGC_ERR_INVALID;
+  if (o.worklist == IPGC_WORKLIST_REBUILD && o.driver != IPGC_DRIVER_PERSISTENT)
+    return IPGC_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard g(ctx->device);
   if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);

@@ -52,6 +52,8 @@ struct Ctrl {
   int32_t maxc_start[2];           // largest committed colour at the start of a round, per parity
   int32_t ficnt[2];                // work items of the worklist's filtered nodes, per parity
   int32_t handoff_round;           // first round of neighbour filtering (0: none)
+  int32_t mode_at[2];              // mode of the latest round of each parity
+  int32_t rbcnt[2];                // worklist rebuild: low-degree nodes, work items
   int32_t pad[2];
   // arrival counters of the grid barrier's groups, one 32-byte sector each
   uint32_t bar_grp[kBarGroups][8];
@@ -106,6 +108,7 @@ struct Params {
   int32_t filt_deg;
   int32_t filt_r0;    // host-loop driver: the hand-over round once reached (0: not yet)
   int32_t shrink;     // the team may drop CTAs in small data-driven rounds (single graph)
+  int32_t wl_rebuild; // topology-driven rounds keep no worklist; it is rebuilt on the way back
   int64_t handoff_wl; // hand over when |WL| <= handoff_wl (0: never)
   // Optional result publication into host-mapped pinned memory (nullptr:
   // none). When a graph is done its team copies the colours to out_colors

@@ -29,6 +29,7 @@ struct Smem {
   int red[W];
   int mode_b;  // broadcast of the round's mode (learned policy)
   unsigned red2[W];
+  unsigned red3[W];
 };
 
 template <int BS>
@@ -67,9 +68,10 @@ struct PhaseAcc {
   int maxc = 0;                 // largest colour committed by this thread
   unsigned long long dsum = 0;  // degrees of the nodes this thread pushed
   unsigned long long nbig = 0;  // high-degree nodes this thread pushed
+  unsigned long long nsm = 0;   // low-degree losers counted, not pushed (worklist rebuild)
 };
 
-// One CTA-wide reduction of the three accumulators, then one atomic each.
+// One CTA-wide reduction of the accumulators, then one atomic each.
 template <int BS>
 __device__ __forceinline__ void phase_commit(const Params& p, Smem<BS>& sm, const PhaseAcc& a,
                                              int nxt) {
@@ -77,11 +79,13 @@ __device__ __forceinline__ void phase_commit(const Params& p, Smem<BS>& sm, cons
   const int m = __reduce_max_sync(FULL, a.maxc);
   const unsigned long long ds = warp_sum_u64(a.dsum);
   const unsigned nb = __reduce_add_sync(FULL, (unsigned)a.nbig);
+  const unsigned ns = __reduce_add_sync(FULL, (unsigned)a.nsm);
   __syncthreads();  // previous users of the scratch slots are done
   if (lane == 0) {
     sm.red[warp] = m;
     sm.red64[warp] = ds;
     sm.red2[warp] = nb;
+    sm.red3[warp] = ns;
   }
   __syncthreads();
   if (warp == 0) {
@@ -89,10 +93,12 @@ __device__ __forceinline__ void phase_commit(const Params& p, Smem<BS>& sm, cons
     const int mm = __reduce_max_sync(FULL, in ? sm.red[lane] : 0);
     const unsigned long long dd = warp_sum_u64(in ? sm.red64[lane] : 0ull);
     const unsigned bb = __reduce_add_sync(FULL, in ? sm.red2[lane] : 0u);
+    const unsigned ss = __reduce_add_sync(FULL, in ? sm.red3[lane] : 0u);
     if (lane == 0) {
       if (mm > 0) atomicMax(&p.ctrl->maxc, mm);
       if (dd) atomicAdd(&p.ctrl->dsum[nxt], dd);
       if (bb) atomicAdd(&p.ctrl->cnt[nxt][B_BIG], (int)bb);
+      if (ss) atomicAdd(&p.ctrl->cnt[nxt][B_SMALL], (int)ss);
     }
   }
 }
@@ -127,7 +133,10 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm) {
       if (lose) acc.dsum += (unsigned long long)d;
     }
     const bool big = valid && bucket_of(d, p.t1) == B_BIG;
-    stage_push(ss, kStageSmall, lose && !big, v, p.wl[0], &c->cnt[0][B_SMALL]);
+    // round 1 is topology-driven: with worklist rebuild its losers are counted, not pushed
+    const bool keep = !p.wl_rebuild;
+    stage_push(ss, kStageSmall, keep && lose && !big, v, p.wl[0], &c->cnt[0][B_SMALL]);
+    if (!keep && lose && !big) acc.nsm += 1;
     const int nch = big ? num_chunks(d, p.chunk) : 0;
     const bool multi = nch > 1;  // (every node that can be filtered is one of them)
     const unsigned mm = __ballot_sync(FULL, multi);
@@ -145,7 +154,7 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm) {
       }
     }
     items_push(st, v, nch, gslot, p.istat, &c->nistat);
-    items_push(si, v, lose ? nch : 0, gslot, p.items[0], &c->icnt[0]);
+    items_push(si, v, keep && lose ? nch : 0, gslot, p.items[0], &c->icnt[0]);
     if (big && lose) acc.nbig += 1;
   }
   stage_flush(ss, p.wl[0], &c->cnt[0][B_SMALL]);
@@ -459,7 +468,7 @@ __device__ __forceinline__ void item_assign(const Params& p, unsigned* wb, int v
 // commits v or pushes its items to the next worklist.
 __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, int v, int s, int d,
                                             int c, int nch, int gslot, int nxt, PhaseAcc& acc,
-                                            int round) {
+                                            int round, bool push = true) {
   const int lane = lane_id();
   const uint64_t pol = l2_keep_policy();
   const int t = ld_cg(p.tent + v);
@@ -509,7 +518,7 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
     finisher = __shfl_sync(FULL, finisher, 0);
     lose = __shfl_sync(FULL, lose, 0);
   }
-  items_push(stage, v, (finisher && lose && lane == 0) ? nch : 0, gslot, p.items[nxt],
+  items_push(stage, v, (push && finisher && lose && lane == 0) ? nch : 0, gslot, p.items[nxt],
              &p.ctrl->icnt[nxt]);
   if (finisher && lane == 0) {
     if (lose) {
@@ -939,6 +948,11 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
   c->dsum[nxt] = 0;
   c->rounds = r;
   c->maxc_start[r & 1] = rv.maxc;
+  c->mode_at[r & 1] = rv.mode;
+  if (rv.mode == MODE_TOPO) {  // a later rebuild counts from zero
+    c->rbcnt[0] = 0;
+    c->rbcnt[1] = 0;
+  }
   if (rv.mode == MODE_TOPO)
     c->rounds_topo += 1;
   else
@@ -1052,9 +1066,10 @@ __device__ __forceinline__ PhaseAcc detect_items(const Params& p, ItemStage& sta
   const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   PhaseAcc acc;
+  const bool push = !(topo && p.wl_rebuild);  // rebuild: topology sweeps keep no worklist
   for_items(p, items, count, topo, gwarp, nwarps, INT_MAX,
             [&](int v, int cidx, int gslot, int nch, int s, int d) {
-              item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round);
+              item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round, push);
             });
   return acc;
 }
@@ -1126,13 +1141,15 @@ __device__ __forceinline__ PhaseAcc detect_small_nodes(const Params& p, Smem<BS>
   unsigned* wm = sm.small_w[warp];
   WarpStage sg{sm.stage_s[warp], 0};
   const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
+  const bool push = !(topo && p.wl_rebuild);  // rebuild: topology sweeps keep no worklist
   for_small<true>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
                   [&](int v, int s, int d, int t) {
                     const bool lose = small_lose(p, v, s, d, t, wm);
-                    stage_push(sg, kStageSmall, v >= 0 && lose, v, p.wl[nxt],
+                    stage_push(sg, kStageSmall, push && v >= 0 && lose, v, p.wl[nxt],
                                &c->cnt[nxt][B_SMALL]);
                     if (v >= 0) {
                       if (lose) {
+                        if (!push) acc.nsm += 1;
                         acc.dsum += (unsigned long long)d;
                       } else {
                         p.color[v] = t;
@@ -1149,6 +1166,46 @@ __device__ __forceinline__ void acc_merge(PhaseAcc& a, const PhaseAcc& b) {
   a.maxc = max(a.maxc, b.maxc);
   a.dsum += b.dsum;
   a.nbig += b.nbig;
+  a.nsm += b.nsm;
+}
+
+// Worklist rebuild (the discard-and-rebuild hybrid of Nasre et al., which the
+// paper contrasts with its own, Section I): a data-driven round that follows
+// a topology-driven one, which kept no worklist, first collects the active
+// nodes: every low-degree node of colour 0 into the low-degree list, every
+// static work item of an active high-degree node into the item list, with
+// counts in rbcnt; a team barrier follows.
+template <int BS>
+__device__ __noinline__ void rebuild_worklists(const Params& p, Smem<BS>& sm, const RoundView& rv,
+                                               Team tm) {
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
+  Ctrl* c = p.ctrl;
+  WarpStage sg{sm.stage_s[warp], 0};
+  for (int64_t base = (int64_t)gwarp * 32; base < p.n; base += (int64_t)nwarps * 32) {
+    const int v = (int)(base + lane);
+    bool act = false;
+    if (v < p.n && ld_cg(p.color + v) == 0) {
+      const int d = ld_ro(p.rowptr + v + 1) - ld_ro(p.rowptr + v);
+      act = bucket_of(d, p.t1) == B_SMALL;
+    }
+    stage_push(sg, kStageSmall, act, v, p.wl[rv.par], &c->rbcnt[0]);
+  }
+  stage_flush(sg, p.wl[rv.par], &c->rbcnt[0]);
+  ItemStage st{sm.stage_i[warp], 0};
+  for (int64_t k0 = (int64_t)gwarp * 32; k0 < rv.nistat; k0 += (int64_t)nwarps * 32) {
+    const int64_t k = k0 + lane;
+    int4 it = make_int4(0, 0, -1, 0);
+    bool act = false;
+    if (k < rv.nistat) {
+      it = ld_cg4(p.istat + k);
+      act = ld_cg(p.color + it.x) == 0;
+    }
+    // one item at a time, in the static list's order (items of a node are
+    // pushed by its item 0 together, so each node's items stay one group)
+    items_push(st, it.x, act && it.y == 0 ? it.w : 0, it.z, p.items[rv.par], &c->rbcnt[1]);
+  }
+  items_flush(st, p.items[rv.par], &c->rbcnt[1]);
 }
 
 template <int BS, bool FILT>
@@ -1259,6 +1316,13 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       break;
     }
     rv.mode = decide_mode_block<BS>(p, rv, total, sm);
+    if (p.wl_rebuild && rv.mode == MODE_DATA &&
+        (r == 2 || ld_cg(&c->mode_at[(r - 1) & 1]) == MODE_TOPO)) {
+      rebuild_worklists<BS>(p, sm, rv, tm);
+      if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+      rv.nsmall = ld_cg(&c->rbcnt[0]);
+      rv.icnt = ld_cg(&c->rbcnt[1]);
+    }
     if (p.shrink && rv.mode == MODE_DATA && tm.ncta > kShrinkMin) {
       // a small round on a big team costs mostly barriers and idle passes:
       // once a quarter of the team would do with one work unit (an item or

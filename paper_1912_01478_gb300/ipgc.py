@@ -35,6 +35,7 @@ NOALLOC_MAX_NNZ = 8388608
 MODE_THRESHOLD, MODE_TOPO, MODE_DATA, MODE_LEARNED = 0, 1, 2, 3
 DRIVER_PERSISTENT, DRIVER_HOSTLOOP = 0, 1
 PUSH_WL, PUSH_NOWL, PUSH_HYBRID = 0, 1, 2
+WORKLIST_KEEP, WORKLIST_REBUILD = 0, 1
 MODES = {"threshold": MODE_THRESHOLD, "topo": MODE_TOPO, "data": MODE_DATA, "learned": MODE_LEARNED}
 DRIVERS = {"persistent": DRIVER_PERSISTENT, "hostloop": DRIVER_HOSTLOOP}
 
@@ -108,7 +109,7 @@ class Options(ctypes.Structure):
         ("policy_margin", ctypes.c_float),
         ("filter_degree", ctypes.c_int32),
         ("filter_start", ctypes.c_float),
-        ("reserved3", ctypes.c_int32),
+        ("worklist", ctypes.c_int32),
     ]
 
 
@@ -183,6 +184,7 @@ class ColorOptions:
     policy_margin: float = 0.05
     filter_degree: int = 0  # 0: library default; < 0: neighbour filtering off
     filter_start: float = 0.0  # 0: library default
+    worklist: str = "keep"  # "keep" (the paper's hybrid) or "rebuild" (discard and rebuild)
 
     def to_c(self, trace_ptr: int = 0, trace_cap: int = 0, fin_ptr: int = 0) -> Options:
         o = Options()
@@ -202,6 +204,7 @@ class ColorOptions:
         o.policy_margin = self.policy_margin
         o.filter_degree = self.filter_degree
         o.filter_start = self.filter_start
+        o.worklist = {"keep": WORKLIST_KEEP, "rebuild": WORKLIST_REBUILD}[self.worklist]
         return o
 
 

@@ -364,3 +364,65 @@ def test_full_size_workloads(ctx, name):
     for kw in (dict(mode="data"), dict(mode="topo"), dict(driver="hostloop")):
         got2, st2 = gpu_color(ctx, rp, cl, validate=False, **kw)
         assert np.array_equal(got2, got) and st2.rounds == st.rounds
+
+
+@pytest.mark.parametrize("graph", ["rmat", "road", "er"])
+def test_worklist_rebuild(ctx, graph, er_graph):
+    # the discard-and-rebuild hybrid (Section I) gives the same colours: for
+    # every threshold, mode and bucket split
+    rp, cl = {"rmat": lambda: graphgen.rmat(14, 16, seed=22), "road": lambda: graphgen.road(300, seed=23),
+              "er": lambda: er_graph}[graph]()
+    ref = oracle.color(rp, cl)
+    for frac in (0.6, 0.2, 0.0, 1.0):
+        for mode in ("threshold", "topo", "data"):
+            assert_parity(ctx, rp, cl, ref, mode=mode, threshold_frac=frac, worklist="rebuild")
+    for t1, chunk in ((1, 32), (63, 4096), (8, 100)):
+        assert_parity(ctx, rp, cl, ref, t1=t1, chunk=chunk, threshold_frac=0.3, worklist="rebuild")
+
+
+def band_network(lo, hi, k=200.0):
+    """A learned-switch network (8 -> 16 -> 16 -> 1) that says 'topology' iff
+    the largest colour lies in a band: feature 7 = maxc / (maxc + 64) in
+    (lo, hi). Layer 1: tanh(k (f7 - lo)), tanh(k (f7 - hi)); layer 2:
+    tanh((h0 - h1) / 2); output 10 (h2 - 0.38)."""
+    w = np.zeros(433, np.float32)
+    W1, B1, W2, B2, W3, B3 = 0, 128, 144, 400, 416, 432
+    w[W1 + 0 * 8 + 7], w[B1 + 0] = k, -k * lo
+    w[W1 + 1 * 8 + 7], w[B1 + 1] = k, -k * hi
+    w[W2 + 0 * 16 + 0], w[W2 + 0 * 16 + 1] = 0.5, -0.5
+    w[W3 + 0], w[B3] = 10.0, -3.8
+    return w
+
+
+def test_worklist_rebuild_many_switches(ctx):
+    # topology-driven rounds in a band of colours in the middle of the run:
+    # topology (round 1), data (rebuild), topology (discard), data (rebuild)
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc, policy
+
+    rp, cl = graphgen.rmat(14, 16, seed=24)
+    ref = oracle.color(rp, cl)
+    lo, hi = 20 / 84, 40 / 104  # maxc in (20, 40)
+    policy.load(ctx, band_network(lo, hi))
+    try:
+        drp, dcl = to_dev(rp, cl)
+        tr = ipgc.trace_buffer(ref.rounds + 2)
+        for wl in ("rebuild", "keep"):
+            colors, st = ctx.color(drp, dcl, trace=tr,
+                                   options=ipgc.ColorOptions(mode="learned", worklist=wl))
+            assert np.array_equal(colors.cpu().numpy(), ref.colors) and st.rounds == ref.rounds
+            modes = ipgc.read_trace(tr, st.rounds)["mode"]
+            switches = int(np.sum(modes[1:] != modes[:-1]))
+            assert switches >= 3, modes  # topo -> data -> topo -> data at least
+    finally:
+        policy.load(ctx, None)
+
+
+def test_worklist_rebuild_needs_the_persistent_driver(ctx):
+    from paper_1912_01478_gb300 import ipgc
+
+    rp, cl = graphgen.er(500, 1500, seed=5)
+    with pytest.raises(ipgc.IpgcError) as ei:
+        gpu_color(ctx, rp, cl, worklist="rebuild", driver="hostloop")
+    assert ei.value.code == ipgc.IPGC_ERR_UNSUPPORTED
