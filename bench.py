@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000",
                     help="request rates of the serving leg (empty = skip)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--suite", type=int, default=0,
+                    help="Table III analogue on the ten stand-in graphs (slow; 1 = run)")
     ap.add_argument("--worklist-leg", type=int, default=1,
                     help="compare the kept and the rebuilt worklist (0 = skip)")
     ap.add_argument("--micro-n", type=int, default=50_912_018,
@@ -207,6 +209,66 @@ def worklist_leg(args, ctx, drp, dcl, stream):
         row["rebuild_over_keep"] = row["rebuild"]["ms"] / row["keep"]["ms"]
         out.append(row)
     return {"workload": "the headline RMAT scale-22 graph", "filter": "off for both", "rows": out}
+
+
+def suite_leg(args, ctx, stream):
+    """Table III analogue: the stand-ins for the paper's ten graphs (Table I
+    shapes, see graphgen.SUITE), each coloured by Plain (every round
+    data-driven) and Hybrid (the paper's threshold rule), both without
+    neighbour filtering, and by Hybrid with filtering (this build's default);
+    best of 3 colourings each (CUDA events). All three colourings must be
+    identical (the mode never changes a colour) and proper."""
+    import torch
+
+    from paper_1912_01478_gb300 import graphgen, ipgc
+
+    if not args.suite:
+        return None
+    rows = []
+    for name in graphgen.SUITE:
+        t0 = time.perf_counter()
+        rp, cl = graphgen.suite_graph(name)
+        gen_s = time.perf_counter() - t0
+        deg = np.diff(rp)
+        drp = torch.from_numpy(rp).cuda()
+        dcl = torch.from_numpy(cl).cuda()
+        if ctx.validate(drp, dcl, stream=stream) != ipgc.IPGC_OK:
+            raise SystemExit(f"{name}: generated graph failed validation")
+        row = {"graph": name, "n": int(rp.size - 1), "nnz": int(cl.size),
+               "deg_min_med_max": [int(deg.min()), int(np.median(deg)), int(deg.max())],
+               "generation_s": gen_s}
+        ref = None
+        for label, kw in (("plain", dict(mode="data", filter_degree=-1)),
+                          ("hybrid", dict(filter_degree=-1)),
+                          ("hybrid_filtered", dict())):
+            o = ipgc.ColorOptions(validate=False, **kw)
+            colors, st = ctx.color(drp, dcl, options=o, stream=stream)
+            ts = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.color(drp, dcl, colors, options=o, stream=stream, wait=False)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            h = colors.cpu().numpy()
+            if ref is None:
+                ref = h
+                src = np.repeat(np.arange(rp.size - 1), deg)
+                if np.any(h[src] == h[cl]) or h.min(initial=1) < 1:
+                    raise SystemExit(f"{name}: improper colouring")
+            elif not np.array_equal(ref, h):
+                raise SystemExit(f"{name}: {label} coloured differently")
+            row[label] = {"ms": min(ts), "rounds": int(st.rounds), "colors": int(st.num_colors),
+                          "rounds_topo": int(st.rounds_topo)}
+        row["hybrid_over_plain"] = row["plain"]["ms"] / row["hybrid"]["ms"]
+        row["filtered_over_plain"] = row["plain"]["ms"] / row["hybrid_filtered"]["ms"]
+        rows.append(row)
+        del drp, dcl
+        torch.cuda.empty_cache()
+    geo = lambda k: float(np.exp(np.mean([np.log(r[k]) for r in rows])))
+    return {"graphs": rows, "geomean_hybrid_over_plain": geo("hybrid_over_plain"),
+            "geomean_filtered_over_plain": geo("filtered_over_plain")}
 
 
 def micro_leg(args, ctx):
@@ -686,6 +748,7 @@ def main():
         del drp, dcl, colors
         torch.cuda.empty_cache()
         batched_out = batched_leg(args, ctx, dev, stream)
+    suite_out = suite_leg(args, ctx, stream) if world == 1 else None
     micro_out = None
     if world == 1 and args.micro_n > 0:
         torch.cuda.empty_cache()
@@ -756,6 +819,7 @@ def main():
         "serving": serving_out,
         "micro_benchmark": micro_out,
         "worklist_policy": worklist_out,
+        "suite": suite_out,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

@@ -73,6 +73,9 @@ def _load():
     lib.gg_rmat.argtypes = [u64, i32, i64, dbl, dbl, dbl, i32, i32, P(_Csr)]
     lib.gg_road.argtypes = [u64, i32, dbl, dbl, P(_Csr)]
     lib.gg_from_edges.argtypes = [i32, i64, P(i32), P(i32), P(_Csr)]
+    lib.gg_rgg.argtypes = [u64, i32, i32, dbl, P(_Csr)]
+    lib.gg_lattice3.argtypes = [i32, i32, P(_Csr)]
+    lib.gg_hubs.argtypes = [u64, i32, i64, i32, i64, dbl, P(_Csr)]
     lib.gg_batch.argtypes = [u64, i32, i32, i32, dbl, dbl, i32, dbl, dbl, dbl, P(_Batch)]
     lib.gg_free_csr.argtypes = [P(_Csr)]
     lib.gg_free_batch.argtypes = [P(_Batch)]
@@ -81,7 +84,8 @@ def _load():
     lib.gg_derive_seed.argtypes = [u64, u64]
     lib.gg_derive_seed.restype = u64
     lib.gg_num_threads.restype = ctypes.c_int
-    for f in (lib.gg_er, lib.gg_rmat, lib.gg_road, lib.gg_from_edges, lib.gg_batch):
+    for f in (lib.gg_er, lib.gg_rmat, lib.gg_road, lib.gg_from_edges, lib.gg_batch, lib.gg_rgg,
+              lib.gg_lattice3, lib.gg_hubs):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -126,6 +130,29 @@ def road(side: int, seed: int, p_delete: float = 0.30, frac_long: float = 0.01):
     """side x side grid, p_delete of edges removed, frac_long long-range edges added."""
     c = _Csr()
     _check(_load().gg_road(seed, side, p_delete, frac_long, ctypes.byref(c)), "road")
+    return _take(c)
+
+
+def rgg(n: int, dim: int, avg_degree: float, seed: int):
+    """Random geometric graph in the unit square (dim 2) or cube (dim 3), mean
+    degree avg_degree away from the border, IDs in grid-cell order."""
+    c = _Csr()
+    _check(_load().gg_rgg(seed, n, dim, avg_degree, ctypes.byref(c)), "rgg")
+    return _take(c)
+
+
+def lattice3(side: int, r2: int):
+    """side^3 lattice, edges between nodes at squared distance <= r2 (r2 = 6:
+    80 neighbours inside)."""
+    c = _Csr()
+    _check(_load().gg_lattice3(side, r2, ctypes.byref(c)), "lattice3")
+    return _take(c)
+
+
+def hubs(n: int, m_base: int, nhubs: int, max_deg: int, alpha: float, seed: int):
+    """Uniform base of m_base pairs plus nhubs hubs of degree max_deg / (h+1)^alpha."""
+    c = _Csr()
+    _check(_load().gg_hubs(seed, n, m_base, nhubs, max_deg, alpha, ctypes.byref(c)), "hubs")
     return _take(c)
 
 
@@ -208,6 +235,41 @@ def batch_workload(num_graphs: int = 4096, seed: int = 4):
     even index Erdos-Renyi with average degree U(4, 32), odd index RMAT with
     edge factor 8 (IDs permuted), per-graph seeds derived from `seed`."""
     return batch(num_graphs, seed=seed, nmin=100, nmax=200_000, deg_lo=4.0, deg_hi=32.0, rmat_ef=8)
+
+
+# Stand-ins for the paper's ten UFL graphs (Table I: nodes, entries, degree
+# minimum / median / maximum), each built to that shape; `scale` shrinks the
+# node count (and hub sizes) with the degrees kept, for tests.
+SUITE = {
+    # hub-heavy circuit: median degree 4, one hub of ~1.29 M neighbours
+    "circuit5M": lambda s: hubs(int(5_500_000 * s), int(12_000_000 * s), max(1, int(3000 * s)),
+                                int(1_290_500 * s), 0.9, seed=11),
+    # finite-element meshes: regular, median degrees 68 / 44 / 80
+    "Audikw_1": lambda s: rgg(int(943_695 * s), 3, 90.0, seed=12),
+    "Bump_2911": lambda s: rgg(int(2_911_419 * s), 3, 46.0, seed=13),
+    "Queen_4147": lambda s: lattice3(max(2, round(160 * s ** (1 / 3))), 6),
+    # Kronecker (Graph 500) generator, scale 21
+    "kron_g500-logn21": lambda s: rmat(21, 48, seed=14, n_limit=int((1 << 21) * s) if s < 1 else 0),
+    # web crawl: very skewed, IDs in crawl order (not permuted)
+    "indochina-2004": lambda s: rmat(23, 24, seed=15, abc=(0.6, 0.15, 0.15),
+                                     n_limit=int(7_414_866 * s), permute=False),
+    # collaboration graph: dense, moderately skewed
+    "hollywood-2009": lambda s: rmat(21, 55, seed=16, abc=(0.45, 0.22, 0.22),
+                                     n_limit=int(1_139_905 * s)),
+    # random geometric graph, n = 2^24
+    "rgg_n_2_24_s0": lambda s: rgg(int((1 << 24) * s), 2, 16.0, seed=17),
+    # social network
+    "soc-LiveJournal1": lambda s: rmat(23, 10, seed=18, abc=(0.5, 0.2, 0.2),
+                                       n_limit=int(4_847_571 * s)),
+    # road network: average degree ~2.1, degrees 1..13
+    "europe_osm": lambda s: road(max(2, round(7135 * s ** 0.5)), seed=19, p_delete=0.47,
+                                 frac_long=0.005),
+}
+
+
+def suite_graph(name: str, scale: float = 1.0):
+    """(rowptr, col) of the stand-in for one of the paper's ten graphs."""
+    return SUITE[name](scale)
 
 
 # Named workloads: the paper-shaped synthetic inputs (sizes as stated).

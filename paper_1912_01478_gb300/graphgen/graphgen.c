@@ -405,6 +405,248 @@ int gg_road(uint64_t seed, int32_t side, double p_delete, double frac_long, gg_c
   return rc;
 }
 
+/*
+ * Random geometric graph: n points uniform in the unit square (dim 2) or cube
+ * (dim 3), an edge between every two points at Euclidean distance < r, r set
+ * so the mean degree away from the border is avg_degree (pi r^2 n in 2-D,
+ * 4/3 pi r^3 n in 3-D). Points are numbered in the order of the grid cells of
+ * side >= r they fall in (x fastest, then y, then z), so nearby points have
+ * nearby IDs, as in the rgg graphs of the DIMACS collection. Coordinates come
+ * from per-chunk streams (2^16 points per chunk).
+ */
+int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out) {
+  if (!out || n < 0 || (dim != 2 && dim != 3) || !(avg_degree >= 0)) return GG_ERR_ARG;
+  const double pi = 3.14159265358979323846;
+  const double r = dim == 2 ? sqrt(avg_degree / (pi * (n > 0 ? n : 1)))
+                            : cbrt(3.0 * avg_degree / (4.0 * pi * (n > 0 ? n : 1)));
+  int64_t G = r > 0 ? (int64_t)floor(1.0 / r) : 1;
+  if (G < 1) G = 1;
+  if (dim == 2 && G > 46340) G = 46340;
+  if (dim == 3 && G > 1290) G = 1290;
+  const int64_t ncell = dim == 2 ? G * G : G * G * G;
+  double* pt = (double*)malloc(sizeof(double) * (size_t)dim * (size_t)(n > 0 ? n : 1));
+  double* sp = (double*)malloc(sizeof(double) * (size_t)dim * (size_t)(n > 0 ? n : 1));
+  int64_t* cell = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* cstart = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+  int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
+  if (!pt || !sp || !cell || !cstart || !cnt) {
+    free(pt); free(sp); free(cell); free(cstart); free(cnt);
+    return GG_ERR_OOM;
+  }
+  const int64_t chunk = 1 << 16, nch = ((int64_t)n + chunk - 1) / chunk;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < nch; ++k) {
+    rng_t rr;
+    rng_seed(&rr, gg_derive_seed(seed, (uint64_t)k));
+    const int64_t hi = (k + 1) * chunk < n ? (k + 1) * chunk : n;
+    for (int64_t i = k * chunk; i < hi; ++i) {
+      int64_t c = 0, mul = 1;
+      for (int d = 0; d < dim; ++d) {
+        const double x = rng_unit(&rr);
+        pt[i * dim + d] = x;
+        int64_t q = (int64_t)(x * (double)G);
+        if (q >= G) q = G - 1;
+        c += q * mul;
+        mul *= G;
+      }
+      cell[i] = c;
+    }
+  }
+  /* counting sort by cell: the new ID of point i is its place in cell order */
+  for (int64_t i = 0; i < n; ++i) cstart[cell[i] + 1]++;
+  for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+  {
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+    if (!fill) {
+      free(pt); free(sp); free(cell); free(cstart); free(cnt);
+      return GG_ERR_OOM;
+    }
+    memcpy(fill, cstart, sizeof(int64_t) * (size_t)ncell);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t k = fill[cell[i]]++;
+      for (int d = 0; d < dim; ++d) sp[k * dim + d] = pt[i * dim + d];
+    }
+    free(fill);
+  }
+  free(pt);
+  /* pairs (i, j), j > i, at distance < r: count per point, then emit */
+  const double r2 = r * r;
+  for (int pass = 0; pass < 2; ++pass) {
+    int32_t* src = NULL;
+    int32_t* dst = NULL;
+    if (pass == 1) {
+      cnt[0] = 0;
+      for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+      src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
+      dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
+      if (!src || !dst) {
+        free(src); free(dst); free(sp); free(cell); free(cstart); free(cnt);
+        return GG_ERR_OOM;
+      }
+    }
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t q[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) {
+        q[d] = (int64_t)(sp[i * dim + d] * (double)G);
+        if (q[d] >= G) q[d] = G - 1;
+      }
+      int64_t k = 0, w = pass ? cnt[i] : 0;
+      const int64_t zlo = dim == 3 ? -1 : 0, zhi = dim == 3 ? 1 : 0;
+      for (int64_t dz = zlo; dz <= zhi; ++dz)
+        for (int64_t dy = -1; dy <= 1; ++dy)
+          for (int64_t dx = -1; dx <= 1; ++dx) {
+            const int64_t cx = q[0] + dx, cy = q[1] + dy, cz = q[2] + dz;
+            if (cx < 0 || cy < 0 || cz < 0 || cx >= G || cy >= G || (dim == 3 && cz >= G)) continue;
+            const int64_t c = cx + G * (cy + G * cz);
+            for (int64_t j = cstart[c] > i + 1 ? cstart[c] : i + 1; j < cstart[c + 1]; ++j) {
+              double s2 = 0;
+              for (int d = 0; d < dim; ++d) {
+                const double t = sp[j * dim + d] - sp[i * dim + d];
+                s2 += t * t;
+              }
+              if (s2 < r2) {
+                if (pass) {
+                  src[w] = (int32_t)i;
+                  dst[w] = (int32_t)j;
+                  ++w;
+                }
+                ++k;
+              }
+            }
+          }
+      if (!pass) cnt[i + 1] = k;
+    }
+    if (pass == 1) {
+      const int64_t m = cnt[n];
+      free(sp); free(cell); free(cstart); free(cnt);
+      const int rc = build_csr(n, m, src, dst, out);
+      free(src);
+      free(dst);
+      return rc;
+    }
+  }
+  return GG_ERR_ARG;  /* not reached */
+}
+
+/*
+ * 3-D lattice of side^3 nodes (ID = x + side * (y + side * z)), an edge
+ * between two nodes whose offset (dx, dy, dz) has dx^2 + dy^2 + dz^2 <= r2;
+ * r2 = 6 gives 80 neighbours inside the lattice (fewer at the faces), the
+ * degree profile of a regular 3-D finite-element mesh.
+ */
+int gg_lattice3(int32_t side, int32_t r2, gg_csr* out) {
+  if (!out || side < 0 || side > 1290 || r2 < 1 || r2 > 16) return GG_ERR_ARG;
+  int off[400][3];
+  int no = 0;
+  const int R = (int)floor(sqrt((double)r2));
+  for (int dz = -R; dz <= R; ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx) {
+        if (dx * dx + dy * dy + dz * dz > r2) continue;
+        /* one of each +-pair: the lexicographically positive (dz, dy, dx) */
+        if (dz < 0 || (dz == 0 && (dy < 0 || (dy == 0 && dx <= 0)))) continue;
+        off[no][0] = dx;
+        off[no][1] = dy;
+        off[no][2] = dz;
+        ++no;
+      }
+  const int64_t n = (int64_t)side * side * side;
+  if (n > INT32_MAX) return GG_ERR_TOO_BIG;
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!cnt) return GG_ERR_OOM;
+  for (int pass = 0; pass < 2; ++pass) {
+    int32_t* src = NULL;
+    int32_t* dst = NULL;
+    if (pass == 1) {
+      for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+      src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
+      dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
+      if (!src || !dst) {
+        free(src); free(dst); free(cnt);
+        return GG_ERR_OOM;
+      }
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < n; ++v) {
+      const int64_t x = v % side, y = (v / side) % side, z = v / ((int64_t)side * side);
+      int64_t k = 0, w = pass ? cnt[v] : 0;
+      for (int o = 0; o < no; ++o) {
+        const int64_t X = x + off[o][0], Y = y + off[o][1], Z = z + off[o][2];
+        if (X < 0 || Y < 0 || Z < 0 || X >= side || Y >= side || Z >= side) continue;
+        if (pass) {
+          src[w] = (int32_t)v;
+          dst[w] = (int32_t)(X + side * (Y + (int64_t)side * Z));
+          ++w;
+        }
+        ++k;
+      }
+      if (!pass) cnt[v + 1] = k;
+    }
+    if (pass == 1) {
+      const int64_t m = cnt[n];
+      free(cnt);
+      const int rc = build_csr((int32_t)n, m, src, dst, out);
+      free(src);
+      free(dst);
+      return rc;
+    }
+  }
+  return GG_ERR_ARG;  /* not reached */
+}
+
+/*
+ * Hub-heavy graph: m_base uniform pairs over n nodes (an Erdos-Renyi-like
+ * base; self-loops and repeats dropped by the CSR build), plus nhubs hubs,
+ * hub h (a uniform node) joined to round(max_deg / (h + 1)^alpha) uniform
+ * nodes. Every stream is per chunk of 2^16 draws or per hub.
+ */
+int gg_hubs(uint64_t seed, int32_t n, int64_t m_base, int32_t nhubs, int64_t max_deg, double alpha,
+            gg_csr* out) {
+  if (!out || n < 1 || m_base < 0 || nhubs < 0 || max_deg < 0 || !(alpha >= 0)) return GG_ERR_ARG;
+  int64_t* hstart = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nhubs + 1));
+  if (!hstart) return GG_ERR_OOM;
+  hstart[0] = m_base;
+  for (int32_t h = 0; h < nhubs; ++h) {
+    int64_t d = (int64_t)llround((double)max_deg / pow((double)(h + 1), alpha));
+    if (d > n - 1) d = n - 1;
+    hstart[h + 1] = hstart[h] + d;
+  }
+  const int64_t m = hstart[nhubs];
+  int32_t* src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  int32_t* dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  if (!src || !dst) {
+    free(src); free(dst); free(hstart);
+    return GG_ERR_OOM;
+  }
+  const int64_t chunk = 1 << 16, nch = (m_base + chunk - 1) / chunk;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < nch; ++k) {
+    rng_t rr;
+    rng_seed(&rr, gg_derive_seed(seed, (uint64_t)k));
+    const int64_t hi = (k + 1) * chunk < m_base ? (k + 1) * chunk : m_base;
+    for (int64_t e = k * chunk; e < hi; ++e) {
+      src[e] = (int32_t)rng_below(&rr, (uint64_t)n);
+      dst[e] = (int32_t)rng_below(&rr, (uint64_t)n);
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t h = 0; h < nhubs; ++h) {
+    rng_t rr;
+    rng_seed(&rr, gg_derive_seed(seed ^ 0x68756273ULL, (uint64_t)h));
+    const int32_t hub = (int32_t)rng_below(&rr, (uint64_t)n);
+    for (int64_t e = hstart[h]; e < hstart[h + 1]; ++e) {
+      src[e] = hub;
+      dst[e] = (int32_t)rng_below(&rr, (uint64_t)n);
+    }
+  }
+  free(hstart);
+  const int rc = build_csr(n, m, src, dst, out);
+  free(src);
+  free(dst);
+  return rc;
+}
+
 void gg_free_csr(gg_csr* g) {
   if (!g) return;
   free(g->rowptr);

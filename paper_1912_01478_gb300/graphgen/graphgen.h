@@ -36,6 +36,10 @@ int gg_er(uint64_t seed, int32_t n, int64_t m, gg_csr* out);
 int gg_rmat(uint64_t seed, int32_t scale, int64_t nedges, double a, double b, double c,
             int32_t n_limit, int32_t permute, gg_csr* out);
 int gg_road(uint64_t seed, int32_t side, double p_delete, double frac_long, gg_csr* out);
+int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out);
+int gg_lattice3(int32_t side, int32_t r2, gg_csr* out);
+int gg_hubs(uint64_t seed, int32_t n, int64_t m_base, int32_t nhubs, int64_t max_deg, double alpha,
+            gg_csr* out);
 int gg_batch(uint64_t seed, int32_t num_graphs, int32_t nmin, int32_t nmax, double deg_lo,
              double deg_hi, int32_t rmat_ef, double a, double b, double c, gg_batch_t* out);
 void gg_free_csr(gg_csr* g);
