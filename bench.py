@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--suite", type=int, default=0,
                     help="Table III analogue on the ten stand-in graphs (slow; 1 = run)")
+    ap.add_argument("--mode-rules", type=int, default=1,
+                    help="compare per-round mode rules on held-out graphs (0 = skip)")
     ap.add_argument("--worklist-leg", type=int, default=1,
                     help="compare the kept and the rebuilt worklist (0 = skip)")
     ap.add_argument("--micro-n", type=int, default=50_912_018,
@@ -269,6 +271,43 @@ def suite_leg(args, ctx, stream):
     geo = lambda k: float(np.exp(np.mean([np.log(r[k]) for r in rows])))
     return {"graphs": rows, "geomean_hybrid_over_plain": geo("hybrid_over_plain"),
             "geomean_filtered_over_plain": geo("filtered_over_plain")}
+
+
+def mode_rules_leg(args, ctx):
+    """Per-round mode rules on held-out graphs (the ten suite stand-ins at 5 %
+    scale), from forced-mode round times: the paper's H = 0.6 n, the byte
+    model's H (policy.BYTES_KAPPA), a threshold fitted to training graphs,
+    the learned switch trained on the same training graphs, and the
+    per-round best. Totals are summed round times (ns -> ms)."""
+    import torch
+
+    from paper_1912_01478_gb300 import graphgen, policy
+
+    if not args.mode_rules:
+        return None
+    train_specs = [(15, 16, 1), (16, 8, 2), (17, 16, 3), (18, 8, 8)]
+    train_graphs = [graphgen.rmat(a, b, seed=sd) for a, b, sd in train_specs]
+    train_graphs += [graphgen.road(512, seed=4), graphgen.road(1024, seed=5),
+                     graphgen.er(200_000, 800_000, seed=6), graphgen.er(60_000, 960_000, seed=7)]
+    train = policy.collect(ctx, train_graphs)
+    held = policy.collect(ctx, [graphgen.suite_graph(nm, 0.05) for nm in graphgen.SUITE])
+    fit = policy.fit_threshold(train)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    w, _ = policy.train(ctx, dev(train.x), dev(train.y), dev(train.w / max(train.w.mean(), 1e-9)),
+                        epochs=1500, lr=0.01)
+    learned, _ = policy.decisions(w, held.x, 0.05, held.thr_topo)
+    rules = {"paper_0.6": policy.threshold_choices(held, 0.6),
+             "byte_model": policy.threshold_choices(held, policy.BYTES_KAPPA),
+             "fitted": policy.threshold_choices(held, fit=fit),
+             "learned": learned,
+             "all_data": np.zeros(held.wl.size, bool)}
+    out = {k: held.totals(v) / 1e6 for k, v in rules.items()}
+    out["per_round_best"] = float(np.minimum(held.t_topo, held.t_data).sum() / 1e6)
+    a, b, c = fit
+    return {"held_out": "the ten suite stand-ins at 5 % scale", "rounds": int(held.wl.size),
+            "total_round_ms": out, "byte_model_kappa": policy.BYTES_KAPPA,
+            "fitted": {"a_ns_per_node": a, "b_ns_per_wl": b, "c_ns": c,
+                       "H_over_n_at_1M": (a * 1e6 + c) / b / 1e6}}
 
 
 def micro_leg(args, ctx):
@@ -749,6 +788,7 @@ def main():
         torch.cuda.empty_cache()
         batched_out = batched_leg(args, ctx, dev, stream)
     suite_out = suite_leg(args, ctx, stream) if world == 1 else None
+    rules_out = mode_rules_leg(args, ctx) if world == 1 else None
     micro_out = None
     if world == 1 and args.micro_n > 0:
         torch.cuda.empty_cache()
@@ -820,6 +860,7 @@ def main():
         "micro_benchmark": micro_out,
         "worklist_policy": worklist_out,
         "suite": suite_out,
+        "mode_rules": rules_out,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

@@ -135,6 +135,8 @@ class Traces:
     t_data: np.ndarray   # [m] ns, data-driven
     thr_topo: np.ndarray  # [m] bool, the threshold rule's choice
     graph: np.ndarray    # [m] index of the graph
+    nodes: np.ndarray = None  # [m] n of the round's graph
+    wl: np.ndarray = None     # [m] |WL| at the start of the round
 
     @property
     def y(self):
@@ -150,7 +152,8 @@ class Traces:
 
     def subset(self, mask):
         return Traces(self.x[mask], self.t_topo[mask], self.t_data[mask], self.thr_topo[mask],
-                      self.graph[mask])
+                      self.graph[mask], None if self.nodes is None else self.nodes[mask],
+                      None if self.wl is None else self.wl[mask])
 
 
 def _round_times(tr):
@@ -162,7 +165,7 @@ def collect(ctx: "ipgc.Context", graphs, reps: int = 3, threshold_frac: float = 
     runs per mode and round."""
     import torch
 
-    xs, tt, td, thr, gi = [], [], [], [], []
+    xs, tt, td, thr, gi, ns, ws = [], [], [], [], [], [], []
     for g, (rp, cl) in enumerate(graphs):
         n, nnz = rp.size - 1, cl.size
         drp = torch.from_numpy(np.ascontiguousarray(rp, np.int32)).cuda()
@@ -190,9 +193,43 @@ def collect(ctx: "ipgc.Context", graphs, reps: int = 3, threshold_frac: float = 
         td.append(times["data"][sl])
         thr.append(wl[sl] > int(threshold_frac * n))
         gi.append(np.full(R - 1, g))
+        ns.append(np.full(R - 1, n))
+        ws.append(wl[sl])
     cat = lambda a, dt: np.concatenate(a).astype(dt) if a else np.zeros(0, dt)  # noqa: E731
     return Traces(np.concatenate(xs).astype(np.float32) if xs else np.zeros((0, NIN), np.float32),
-                  cat(tt, np.float64), cat(td, np.float64), cat(thr, bool), cat(gi, np.int32))
+                  cat(tt, np.float64), cat(td, np.float64), cat(thr, bool), cat(gi, np.int32),
+                  cat(ns, np.float64), cat(ws, np.float64))
+
+
+# Analytical thresholds H (Section VII leaves H to be derived analytically).
+#
+# Byte model of one round of this build's kernels. Topology-driven, every node
+# is visited in order: the row offsets and the colour of each node (assign),
+# the row offsets, colour and tentative colour (detect): about 8 + 12 = 20
+# bytes per node, read coalesced. Data-driven, every worklist entry costs its
+# own read (4 bytes per phase) plus random 32-byte sectors for the node's row
+# offsets (each phase) and its tentative colour (detect): about 36 + 68 = 104
+# bytes per active node. The neighbour work is the same in both modes, so
+# topology-driven is cheaper iff 20 n < 104 |WL|.
+BYTES_KAPPA = 20.0 / 104.0
+
+
+def fit_threshold(tr: Traces):
+    """Calibrated model: least squares of t_topo - t_data = a n - b |WL| + c
+    over the rounds of the traces; topology-driven iff |WL| > (a n + c) / b.
+    Returns (a, b, c)."""
+    A = np.stack([tr.nodes, -tr.wl, np.ones_like(tr.wl)], axis=1)
+    coef, *_ = np.linalg.lstsq(A, tr.t_topo - tr.t_data, rcond=None)
+    return tuple(float(v) for v in coef)
+
+
+def threshold_choices(tr: Traces, kappa: float | None = None, fit=None):
+    """Per-round choices (topology = True) of a threshold rule: |WL| > kappa n,
+    or the calibrated rule of fit_threshold's coefficients."""
+    if fit is not None:
+        a, b, c = fit
+        return tr.wl * b > a * tr.nodes + c
+    return tr.wl > kappa * tr.nodes
 
 
 def decisions(w: np.ndarray, x: np.ndarray, margin: float, thr_topo: np.ndarray):

@@ -166,3 +166,33 @@ def test_learned_without_network_is_threshold(ctx):
     _, c = ctx.color(drp, dcl, options=ipgc.ColorOptions(mode="learned"))
     assert c.rounds_data == 0 and c.rounds_topo == c.rounds
     policy.load(ctx, None)
+
+
+def test_analytical_thresholds(ctx):
+    # analytical H (Section VII): the byte model's kappa and a threshold fitted
+    # to forced-mode round times of the training graphs, judged on held-out
+    # graphs against the paper's 0.6 and the per-round best
+    from paper_1912_01478_gb300 import policy
+
+    train = policy.collect(ctx, [make(*g) for g in TRAIN])
+    held = policy.collect(ctx, [make(*g) for g in HELD])
+    fit = policy.fit_threshold(train)
+    a, b, c = fit
+    assert b > 0  # a longer worklist favours the topology-driven round
+    rules = {
+        "paper 0.6": policy.threshold_choices(held, 0.6),
+        "bytes": policy.threshold_choices(held, policy.BYTES_KAPPA),
+        "fitted": policy.threshold_choices(held, fit=fit),
+        "all data": np.zeros(held.wl.size, bool),
+        "all topo": np.ones(held.wl.size, bool),
+    }
+    tot = {k: held.totals(v) for k, v in rules.items()}
+    best = float(np.minimum(held.t_topo, held.t_data).sum())
+    print("\nheld-out round time (ms): " + ", ".join(f"{k} {v / 1e6:.3f}" for k, v in tot.items())
+          + f", per-round best {best / 1e6:.3f}; fitted H/n at n=1e6: {(a * 1e6 + c) / b / 1e6:.3f}")
+    for k, v in tot.items():
+        assert best <= v + 1e-6
+    # the rules are thresholds: topology exactly when the worklist is long
+    assert np.array_equal(rules["bytes"], held.wl > policy.BYTES_KAPPA * held.nodes)
+    # the fitted rule is no worse than the worse fixed policy
+    assert tot["fitted"] <= max(tot["all data"], tot["all topo"]) * 1.001
