@@ -111,8 +111,9 @@ typedef struct ipgc_options {
   int32_t max_rounds;     /* 0 = n + 1, which always suffices */
   uint64_t timeout_ns;    /* limit for each device-side wait; 0 = 10 s */
   int32_t validate;       /* 1 = check the CSR on the device first (IPGC_ERR_INVALID) */
-  int32_t t1;             /* degree <= t1 (<= 63): a warp colours 32 such nodes together;
-                             0 = default 32 */
+  int32_t t1;             /* degree <= t1 (<= 255): a warp colours 32 such nodes together;
+                             0 = chosen on the device: the largest degree when it is <= 255
+                             (every node on the low-degree path), else 64 */
   int32_t chunk;          /* degree > t1: the node's neighbours are cut into work items of
                              this many (32..4096), one warp each; 0 = default 1024 */
   int32_t block_size;     /* threads per CTA of the colouring kernel; 0 = default */

@@ -251,6 +251,7 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.mlp_margin = o.policy_margin;
   p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
   p.shrink = o.driver == IPGC_DRIVER_PERSISTENT ? 1 : 0;
+  p.t1_auto = o.t1 <= 0 ? 1 : 0;  // default t1: chosen on the device
   p.wl_rebuild = o.worklist == IPGC_WORKLIST_REBUILD ? 1 : 0;
 }
 

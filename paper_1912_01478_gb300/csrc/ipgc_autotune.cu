@@ -94,7 +94,7 @@ int ipgc_autotune(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int3
   base.fault_inject = 0;
   std::vector<Knob<ipgc_options>> knobs = {
       {[](ipgc_options& o, int64_t v) { o.chunk = (int32_t)v; }, {256, 512, 1024, 2048, 4096}},
-      {[](ipgc_options& o, int64_t v) { o.t1 = (int32_t)v; }, {8, 16, 24, 40, 63}},
+      {[](ipgc_options& o, int64_t v) { o.t1 = (int32_t)v; }, {16, 32, 64, 128, 255}},
       {[](ipgc_options& o, int64_t v) { o.block_size = (int32_t)v; }, {256, 512}},
   };
   const int rc = descend(
@@ -126,7 +126,7 @@ int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node
   base.base.validate = 0;
   std::vector<Knob<ipgc_batch_options>> knobs = {
       {[](ipgc_batch_options& o, int64_t v) { o.base.chunk = (int32_t)v; }, {512, 1024, 2048}},
-      {[](ipgc_batch_options& o, int64_t v) { o.base.t1 = (int32_t)v; }, {16, 24, 40, 63}},
+      {[](ipgc_batch_options& o, int64_t v) { o.base.t1 = (int32_t)v; }, {16, 32, 64, 128, 255}},
       {[](ipgc_batch_options& o, int64_t v) { o.nnz_per_cta = v; },
        {1 << 14, 1 << 16, 1 << 17, 1 << 18, 1 << 20, (int64_t)1 << 40}},
       {[](ipgc_batch_options& o, int64_t v) { o.max_team = (int32_t)v; }, {0, 4, 16, 64}},

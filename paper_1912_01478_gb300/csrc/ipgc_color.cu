@@ -60,7 +60,10 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) round1_kernel(const __grid
   const uint64_t t0 = gtime();
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctrl->t_start = t0;
   PhaseAcc acc;
-  round1<BS>(p, sm, acc, Team{(int)blockIdx.x, (int)gridDim.x});
+  // with t1 chosen on the device, maxdeg_kernel ran before this launch
+  const int t1 = p.t1_auto ? auto_t1(p, ld_cg(&p.ctrl->maxdeg)) : p.t1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) p.ctrl->t1 = t1;
+  round1<BS>(p, sm, acc, Team{(int)blockIdx.x, (int)gridDim.x}, t1);
   phase_commit<BS>(p, sm, acc, 0);
   if (blockIdx.x == 0 && threadIdx.x == 0) trace_round1(p, t0);
 }
@@ -91,6 +94,16 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) detect_kernel(const __grid
   PhaseAcc acc;
   detect_phase<BS, FILT>(p, sm, rv, acc, Team{(int)blockIdx.x, (int)gridDim.x});
   phase_commit<BS>(p, sm, acc, rv.par ^ 1);
+}
+
+// The largest degree into ctrl->maxdeg (host-loop driver, before round 1).
+__global__ void maxdeg_kernel(Params p) {
+  int m = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, ld_ro(p.rowptr + v + 1) - ld_ro(p.rowptr + v));
+  m = __reduce_max_sync(FULL, m);
+  if (lane_id() == 0 && m > 0) atomicMax(&p.ctrl->maxdeg, m);
 }
 
 __global__ void finish_kernel(Params p, int last_round) {
@@ -182,6 +195,11 @@ cudaError_t launch_persistent(const Params& p, int bs, int blocks, cudaStream_t 
 }
 
 cudaError_t launch_round1(const Params& p, int bs, int blocks, cudaStream_t s) {
+  if (p.t1_auto) {
+    maxdeg_kernel<<<blocks, 256, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   return with_block(bs, [&](auto B) {
     round1_kernel<decltype(B)::value><<<blocks, decltype(B)::value, 0, s>>>(p);
     return cudaGetLastError();

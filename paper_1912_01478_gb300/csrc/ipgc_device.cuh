@@ -18,8 +18,9 @@ constexpr unsigned FULL = 0xffffffffu;
 // completes it.
 enum Bucket : int { B_SMALL = 0, B_BIG = 1, NB = 2 };
 
-constexpr int kMaxT1 = 63;       // 64-bit lane mask covers colours 1..64
-constexpr int kDefaultT1 = 32;
+constexpr int kSmallWords = 8;   // mask words per low-degree node: colours 1..256
+constexpr int kMaxT1 = 32 * kSmallWords - 1;  // degree <= t1 has mex <= 256
+constexpr int kDefaultT1 = 64;  // when some degree exceeds kMaxT1 (t1 chosen automatically)
 constexpr int kDefaultChunk = 1024;
 constexpr int kMinChunk = 32;
 constexpr int kMaxChunk = 4096;
@@ -54,7 +55,8 @@ struct Ctrl {
   int32_t handoff_round;           // first round of neighbour filtering (0: none)
   int32_t mode_at[2];              // mode of the latest round of each parity
   int32_t rbcnt[2];                // worklist rebuild: low-degree nodes, work items
-  int32_t pad[2];
+  int32_t t1;                      // the low-degree bound in use (set before round 1)
+  int32_t maxdeg;                  // largest degree (when t1 is chosen from it)
   // arrival counters of the grid barrier's groups, one 32-byte sector each
   uint32_t bar_grp[kBarGroups][8];
 };
@@ -109,6 +111,7 @@ struct Params {
   int32_t filt_r0;    // host-loop driver: the hand-over round once reached (0: not yet)
   int32_t shrink;     // the team may drop CTAs in small data-driven rounds (single graph)
   int32_t wl_rebuild; // topology-driven rounds keep no worklist; it is rebuilt on the way back
+  int32_t t1_auto;    // choose t1 on the device: the largest degree if <= kMaxT1, else t1
   int64_t handoff_wl; // hand over when |WL| <= handoff_wl (0: never)
   // Optional result publication into host-mapped pinned memory (nullptr:
   // none). When a graph is done its team copies the colours to out_colors

@@ -19,7 +19,7 @@ constexpr int min_blocks(int bs) { return bs >= 512 ? 2 : 3; }
 template <int BS>
 struct Smem {
   static constexpr int W = BS / 32;
-  unsigned small_w[W][64];          // per warp: two mask words per lane / loser flags
+  unsigned small_w[W][32 * kSmallWords];  // per warp: the lanes' colour masks / loser flags
   unsigned wbits[W][kGWords];       // per warp: bitmap of colours 1..2048 (work items)
   int32_t stage_s[W][kStageSmall];  // staged pushes: low-degree losers
   int4 stage_i[W][kStageItems];     // staged pushes: work items of high-degree losers
@@ -35,7 +35,7 @@ struct Smem {
 template <int BS>
 __device__ __forceinline__ void smem_clear(Smem<BS>& sm) {
   unsigned* w = &sm.small_w[0][0];
-  for (int i = threadIdx.x; i < Smem<BS>::W * 64; i += BS) w[i] = 0;
+  for (int i = threadIdx.x; i < Smem<BS>::W * 32 * kSmallWords; i += BS) w[i] = 0;
   w = &sm.wbits[0][0];
   for (int i = threadIdx.x; i < Smem<BS>::W * kGWords; i += BS) w[i] = 0;
   __syncthreads();
@@ -112,7 +112,7 @@ __device__ __forceinline__ int num_chunks(int d, int chunk) { return (d + chunk 
 // the static work items of every high-degree node used by later topology
 // sweeps; hands out merge-state slots to nodes with several items.
 template <int BS>
-__device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm) {
+__device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, int t1) {
   Ctrl* c = p.ctrl;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   WarpStage ss{sm.stage_s[warp], 0};
@@ -132,7 +132,7 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm) {
       if (p.fin) p.fin[v] = lose ? 0 : 1;
       if (lose) acc.dsum += (unsigned long long)d;
     }
-    const bool big = valid && bucket_of(d, p.t1) == B_BIG;
+    const bool big = valid && bucket_of(d, t1) == B_BIG;
     // round 1 is topology-driven: with worklist rebuild its losers are counted, not pushed
     const bool keep = !p.wl_rebuild;
     stage_push(ss, kStageSmall, keep && lose && !big, v, p.wl[0], &c->cnt[0][B_SMALL]);
@@ -202,13 +202,13 @@ __device__ __forceinline__ int small_owner(int off, int e) {
 
 constexpr int kSmallUnroll = 8;
 
-// First-fit colour of each lane's node into tent[v]. wm: this warp's 64 words.
+// First-fit colour of each lane's node into tent[v]. wm: this warp's 32 * kSmallWords words.
 __device__ __forceinline__ void small_assign(const Params& p, int v, int s, int d, unsigned* wm) {
   const int lane = lane_id();
   const uint64_t pol = l2_keep_policy();
   const SmallSeg g = small_scan(d);
-  wm[2 * lane] = 0;
-  wm[2 * lane + 1] = 0;
+#pragma unroll
+  for (int k = 0; k < kSmallWords; ++k) wm[kSmallWords * lane + k] = 0;
   __syncwarp();
   for (int base = 0; base < g.total; base += 32 * kSmallUnroll) {
     int u[kSmallUnroll], j[kSmallUnroll];
@@ -227,14 +227,20 @@ __device__ __forceinline__ void small_assign(const Params& p, int v, int s, int 
 #pragma unroll
     for (int q = 0; q < kSmallUnroll; ++q) {
       const int c = cc[q];
-      if (c >= 1 && c <= 64) atomicOr(&wm[2 * j[q] + ((c - 1) >> 5)], 1u << ((c - 1) & 31));
+      if (c >= 1 && c <= 32 * kSmallWords)
+        atomicOr(&wm[kSmallWords * j[q] + ((c - 1) >> 5)], 1u << ((c - 1) & 31));
     }
   }
   __syncwarp();
   if (v >= 0) {
-    const unsigned long long m =
-        (unsigned long long)wm[2 * lane] | ((unsigned long long)wm[2 * lane + 1] << 32);
-    p.tent[v] = __ffsll((long long)~m);
+    // first free colour: degree <= t1 < 32 * kSmallWords keeps it in the mask
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < kSmallWords; ++k) {
+      const unsigned w = wm[kSmallWords * lane + k];
+      if (t == 0 && w != FULL) t = 32 * k + __ffs(~w);
+    }
+    p.tent[v] = t;
   }
   __syncwarp();
 }
@@ -831,7 +837,7 @@ __device__ __forceinline__ void for_items_plain(const Params& p, const int4* ite
 // t = tent[v] when WithTent).
 template <bool WithTent, class F>
 __device__ __forceinline__ void for_small(const Params& p, const int32_t* list, int64_t span,
-                                          bool topo, int64_t start, int64_t stride, F f) {
+                                          bool topo, int t1, int64_t start, int64_t stride, F f) {
   if (start >= span) return;
   const int lane = lane_id();
   auto node_at = [&](int64_t i) -> int {
@@ -856,7 +862,7 @@ __device__ __forceinline__ void for_small(const Params& p, const int32_t* list, 
     }
     const int vC = node_at(base + 2 * stride + lane);
     int v = vA, d = eA - sA;
-    if (v >= 0 && topo && (d > p.t1 || cA != 0)) v = -1;
+    if (v >= 0 && topo && (d > t1 || cA != 0)) v = -1;
     if (v < 0) d = 0;
     f(v, sA, d, tA);
     vA = vB;
@@ -881,6 +887,7 @@ struct RoundView {
   int ficnt;   // work items of the worklist's filtered nodes
   int maxc;    // largest committed colour at round start
   int r0;      // first round of neighbour filtering (0: not started)
+  int t1;      // the low-degree bound in use
   int filt;    // nodes of degree > filt_deg read filtered lists this round
   unsigned long long dsum;  // degree sum of the worklist
 };
@@ -894,6 +901,7 @@ __device__ __forceinline__ RoundView read_round(const Params& p, int r) {
   rv.icnt = ld_cg(&p.ctrl->icnt[rv.par]);
   rv.nistat = ld_cg(&p.ctrl->nistat);
   rv.ficnt = ld_cg(&p.ctrl->ficnt[rv.par]);
+  rv.t1 = ld_cg(&p.ctrl->t1);
   rv.maxc = ld_cg(&p.ctrl->maxc);
   rv.dsum = __ldcg(&p.ctrl->dsum[rv.par]);
   rv.mode = MODE_DATA;
@@ -1037,7 +1045,7 @@ __device__ __forceinline__ void assign_small_nodes(const Params& p, Smem<BS>& sm
   const bool topo = rv.mode == MODE_TOPO;
   unsigned* wm = sm.small_w[warp];
   const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
-  for_small<false>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
+  for_small<false>(p, p.wl[rv.par], span, topo, rv.t1, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
                    [&](int v, int s, int d, int) { small_assign(p, v, s, d, wm); });
 }
 
@@ -1142,7 +1150,7 @@ __device__ __forceinline__ PhaseAcc detect_small_nodes(const Params& p, Smem<BS>
   WarpStage sg{sm.stage_s[warp], 0};
   const int64_t span = topo ? (int64_t)p.n : (int64_t)rv.nsmall;
   const bool push = !(topo && p.wl_rebuild);  // rebuild: topology sweeps keep no worklist
-  for_small<true>(p, p.wl[rv.par], span, topo, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
+  for_small<true>(p, p.wl[rv.par], span, topo, rv.t1, (int64_t)gwarp * 32, (int64_t)nwarps * 32,
                   [&](int v, int s, int d, int t) {
                     const bool lose = small_lose(p, v, s, d, t, wm);
                     stage_push(sg, kStageSmall, push && v >= 0 && lose, v, p.wl[nxt],
@@ -1187,7 +1195,7 @@ __device__ __noinline__ void rebuild_worklists(const Params& p, Smem<BS>& sm, co
     bool act = false;
     if (v < p.n && ld_cg(p.color + v) == 0) {
       const int d = ld_ro(p.rowptr + v + 1) - ld_ro(p.rowptr + v);
-      act = bucket_of(d, p.t1) == B_SMALL;
+      act = bucket_of(d, rv.t1) == B_SMALL;
     }
     stage_push(sg, kStageSmall, act, v, p.wl[rv.par], &c->rbcnt[0]);
   }
@@ -1295,6 +1303,24 @@ __device__ void publish_result(const Params& p, Team tm) {
 // The whole round loop of one graph by a team of CTAs (the whole grid for the
 // single-graph kernel, a few CTAs or one CTA for a graph of a batch), the
 // rounds separated by the team's bounded barrier.
+// The low-degree bound when it is chosen on the device: every node when all
+// degrees fit the low-degree path (regular graphs: a warp then colours 32
+// nodes with their edges balanced over its lanes), else the given t1.
+__device__ __forceinline__ int auto_t1(const Params& p, int maxdeg) {
+  return maxdeg <= kMaxT1 ? (maxdeg > 0 ? maxdeg : 1) : p.t1;
+}
+
+// The largest degree of the graph into ctrl->maxdeg, then a team barrier.
+template <int BS>
+__device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm) {
+  int m = 0;
+  for (int64_t v = (int64_t)tm.cta * BS + threadIdx.x; v < p.n; v += (int64_t)tm.ncta * BS)
+    m = max(m, ld_ro(p.rowptr + v + 1) - ld_ro(p.rowptr + v));
+  m = block_max<BS>(sm, m);
+  if (threadIdx.x == 0 && m > 0) atomicMax(&p.ctrl->maxdeg, m);
+  return team_barrier(p.ctrl, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
+}
+
 // Rounds r_start, r_start + 1, ... of one graph by a team of CTAs, separated
 // by the team's bounded barrier, until the worklist is empty. Without FILT
 // the loop stops early at the hand-over round (handoff_now), which it
@@ -1360,9 +1386,18 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   const bool lead = tm.cta == 0 && threadIdx.x == 0;
   const uint64_t t0 = gtime();
   if (lead) c->t_start = t0;
+  int t1 = p.t1;
+  if (p.t1_auto) {  // one pass over the row offsets: the largest degree decides t1
+    if (!team_max_degree<BS>(p, sm, tm)) {
+      if (lead) c->t_end = gtime();
+      return;
+    }
+    t1 = auto_t1(p, ld_cg(&c->maxdeg));
+  }
+  if (lead) c->t1 = t1;
   {
     PhaseAcc acc;
-    round1<BS>(p, sm, acc, tm);
+    round1<BS>(p, sm, acc, tm, t1);
     phase_commit<BS>(p, sm, acc, 0);
   }
   if (team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) {

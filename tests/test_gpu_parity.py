@@ -146,7 +146,8 @@ def test_paths(ctx, n):
     assert np.array_equal(got, np.array([1 + i % 2 for i in range(n)])) and st.rounds == n // 2 + 1
 
 
-@pytest.mark.parametrize("t1,chunk", [(0, 0), (1, 32), (3, 64), (8, 100), (63, 4096), (24, 33), (1, 4096)])
+@pytest.mark.parametrize("t1,chunk", [(0, 0), (1, 32), (3, 64), (8, 100), (63, 4096), (24, 33), (1, 4096),
+                                      (128, 1024), (255, 64), (200, 2048)])
 def test_bucket_thresholds(ctx, t1, chunk):
     # the same graph through every split of nodes between the low-degree path
     # and chunked work items, with ragged chunk sizes
