@@ -195,7 +195,8 @@ def worklist_leg(args, ctx, drp, dcl, stream):
     for frac in (0.6, 0.2, 0.05):
         row = {"threshold_frac": frac}
         for wl in ("keep", "rebuild"):
-            o = ipgc.ColorOptions(validate=False, filter_degree=-1, worklist=wl, threshold_frac=frac)
+            o = ipgc.ColorOptions(validate=False, filter_degree=-1, worklist=wl, threshold_frac=frac,
+                                  forbidden="rescan")
             ctx.color(drp, dcl, options=o, stream=stream)
             ts = []
             for _ in range(3):
@@ -210,15 +211,18 @@ def worklist_leg(args, ctx, drp, dcl, stream):
                        "rounds_topo": int(st.rounds_topo), "rounds_data": int(st.rounds_data)}
         row["rebuild_over_keep"] = row["rebuild"]["ms"] / row["keep"]["ms"]
         out.append(row)
-    return {"workload": "the headline RMAT scale-22 graph", "filter": "off for both", "rows": out}
+    return {"workload": "the headline RMAT scale-22 graph",
+            "engine": "rows rescanned every round (the paper's loop), no filtering, for both",
+            "rows": out}
 
 
 def suite_leg(args, ctx, stream):
     """Table III analogue: the stand-ins for the paper's ten graphs (Table I
     shapes, see graphgen.SUITE), each coloured by Plain (every round
-    data-driven) and Hybrid (the paper's threshold rule), both without
-    neighbour filtering, and by Hybrid with filtering (this build's default);
-    best of 3 colourings each (CUDA events). All three colourings must be
+    data-driven) and Hybrid (the paper's threshold rule), both rescanning
+    rows without neighbour filtering (the paper's loop), by Hybrid with
+    filtering, and by Hybrid with forbidden-colour bitmaps (this build's
+    default); best of 3 colourings each (CUDA events). All colourings must be
     identical (the mode never changes a colour) and proper."""
     import torch
 
@@ -240,9 +244,11 @@ def suite_leg(args, ctx, stream):
                "deg_min_med_max": [int(deg.min()), int(np.median(deg)), int(deg.max())],
                "generation_s": gen_s}
         ref = None
-        for label, kw in (("plain", dict(mode="data", filter_degree=-1)),
-                          ("hybrid", dict(filter_degree=-1)),
-                          ("hybrid_filtered", dict())):
+        R = "rescan"
+        for label, kw in (("plain", dict(mode="data", filter_degree=-1, forbidden=R)),
+                          ("hybrid", dict(filter_degree=-1, forbidden=R)),
+                          ("hybrid_filtered", dict(forbidden=R)),
+                          ("hybrid_push", dict())):
             o = ipgc.ColorOptions(validate=False, **kw)
             colors, st = ctx.color(drp, dcl, options=o, stream=stream)
             ts = []
@@ -265,12 +271,14 @@ def suite_leg(args, ctx, stream):
                           "rounds_topo": int(st.rounds_topo)}
         row["hybrid_over_plain"] = row["plain"]["ms"] / row["hybrid"]["ms"]
         row["filtered_over_plain"] = row["plain"]["ms"] / row["hybrid_filtered"]["ms"]
+        row["push_over_plain"] = row["plain"]["ms"] / row["hybrid_push"]["ms"]
         rows.append(row)
         del drp, dcl
         torch.cuda.empty_cache()
     geo = lambda k: float(np.exp(np.mean([np.log(r[k]) for r in rows])))
     return {"graphs": rows, "geomean_hybrid_over_plain": geo("hybrid_over_plain"),
-            "geomean_filtered_over_plain": geo("filtered_over_plain")}
+            "geomean_filtered_over_plain": geo("filtered_over_plain"),
+            "geomean_push_over_plain": geo("push_over_plain")}
 
 
 def mode_rules_leg(args, ctx):

@@ -98,7 +98,8 @@ typedef struct ipgc_trace_rec {
   int32_t max_color;  /* largest committed colour at the start of the round */
   int32_t shortcut;   /* 1 for round 1, whose assignment step is implicit */
   int32_t wl_small;   /* worklist nodes of degree <= t1 */
-  int32_t reserved;
+  int32_t push_ns;    /* IPGC_FORBIDDEN_PUSH: ns of the push phase after the conflict step
+                         (included in t_detect); 0 otherwise */
   uint64_t t_begin;   /* %globaltimer at the start of the round (ns) */
   uint64_t t_assign;  /* ... after the assignment step's grid barrier */
   uint64_t t_detect;  /* ... after the conflict step's grid barrier */
@@ -128,7 +129,8 @@ typedef struct ipgc_options {
   float policy_margin;    /* IPGC_MODE_LEARNED: when the network's probability p of "topology
                              is faster" has |p - 0.5| < policy_margin, or no network is
                              loaded, the threshold rule decides; default 0.05 */
-  int32_t filter_degree;  /* neighbour filtering: once the worklist is small (filter_start),
+  int32_t filter_degree;  /* neighbour filtering (with IPGC_FORBIDDEN_RESCAN; see `forbidden`):
+                             once the worklist is small (filter_start),
                              a node of degree > max(filter_degree, chunk, t1) keeps the list
                              of its still-active neighbours and a bitmap of the colours of
                              its finalised ones, so later rounds read only the active part
@@ -146,10 +148,29 @@ typedef struct ipgc_options {
                              paper compares against, Section I). Same colours either way.
                              REBUILD runs without neighbour filtering and only with the
                              persistent driver (IPGC_ERR_UNSUPPORTED otherwise). */
+  int32_t forbidden;      /* how the assignment step of a node of degree > t1 learns the colours
+                             of its finalised neighbours (its forbidden colours, Section II-C):
+                             IPGC_FORBIDDEN_RESCAN: every round rereads the node's row (the
+                             paper's loop; with neighbour filtering);
+                             IPGC_FORBIDDEN_PUSH: the node keeps a bitmap of those colours, into
+                             which each neighbour ORs its colour once, when it is committed, so
+                             a row is read about once in all instead of once per round; a node
+                             with several work items also keeps the list of its still-active
+                             lower-ID neighbours for its conflict step. Same colours; 12 more
+                             bytes of workspace per entry; needs the persistent driver
+                             (IPGC_ERR_UNSUPPORTED otherwise); turns neighbour filtering off;
+                             rounds that start with a colour above 2046 committed rescan; a
+                             graph without a node of degree > t1 is coloured by rescanning.
+                             IPGC_FORBIDDEN_AUTO (0, default): PUSH with the persistent driver,
+                             RESCAN with the host-loop driver. */
 } ipgc_options;
 
 #define IPGC_WORKLIST_KEEP 0
 #define IPGC_WORKLIST_REBUILD 1
+
+#define IPGC_FORBIDDEN_AUTO 0
+#define IPGC_FORBIDDEN_RESCAN 1
+#define IPGC_FORBIDDEN_PUSH 2
 
 /* Fill *opt with the defaults listed above. */
 IPGC_API void ipgc_options_default(ipgc_options* opt);

@@ -117,44 +117,62 @@ int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
 // A node of degree > t1 has more than t1 entries, so at most nnz / (t1 + 1)
 // exist, with at most nnz / chunk + (their number) items; a node with several
 // items has more than `chunk` entries and a filtered one more than filt_deg.
+//   With pushing (IPGC_FORBIDDEN_PUSH), the list arrays of filtering (lower
+//   parts only, no filtered items) and at the end the forbidden-colour
+//   bitmaps [nnz] words (a node's bitmap inside its own row range), the push
+//   queue [item_cap] and the winners list [n].
 struct WsLayout {
-  size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, fst_bytes, total;
+  size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, fst_bytes, pbits_bytes,
+      pq_bytes, total;
 };
 
 using ipgc::effective_chunk;
 using ipgc::effective_t1;
 
+// Forbidden colours pushed into per-node bitmaps (else rows are rescanned).
+bool effective_push(const ipgc_options& o) {
+  return o.forbidden == IPGC_FORBIDDEN_PUSH ||
+         (o.forbidden == IPGC_FORBIDDEN_AUTO && o.driver == IPGC_DRIVER_PERSISTENT);
+}
+
 // Degree above which a node is filtered (INT32_MAX: off); at least the
 // chunk, so every such node has several work items and a merge-state slot.
 int effective_filt_deg(const ipgc_options& o) {
-  if (o.filter_degree < 0 || o.worklist == IPGC_WORKLIST_REBUILD) return INT32_MAX;
+  if (o.filter_degree < 0 || o.worklist == IPGC_WORKLIST_REBUILD || effective_push(o))
+    return INT32_MAX;
   const int f = o.filter_degree > 0 ? o.filter_degree : ipgc::kDefaultFiltDeg;
   const int lo = effective_chunk(o) > effective_t1(o) ? effective_chunk(o) : effective_t1(o);
   return f > lo ? f : lo;
 }
 
-WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk, int filt_deg) {
+WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk, int filt_deg, bool push) {
   WsLayout L;
   L.a4n = align256((size_t)n * sizeof(int32_t));
   int64_t nbig = nnz / ((int64_t)t1 + 1);
   if (nbig > n) nbig = n;
   const int64_t item_cap = nnz / chunk + nbig + 1;
   const bool filt = filt_deg != INT32_MAX;
+  const bool lists = filt || push;
   const int64_t gcap = nnz / ((int64_t)chunk + 1) + 1;
   L.items_bytes = align256((size_t)item_cap * sizeof(int4));
   L.gbits_bytes = align256((size_t)gcap * ipgc::kGWords * sizeof(uint32_t));
   L.gint_bytes = align256((size_t)gcap * sizeof(int32_t));
-  L.alist_bytes = filt ? align256((size_t)nnz * sizeof(int32_t)) : 0;
-  L.flen_bytes = filt ? align256((size_t)gcap * sizeof(int2)) : 0;
-  L.fst_bytes = filt ? align256((size_t)gcap * sizeof(int32_t)) : 0;
+  L.alist_bytes = lists ? align256((size_t)nnz * sizeof(int32_t)) : 0;
+  L.flen_bytes = lists ? align256((size_t)gcap * sizeof(int2)) : 0;
+  L.fst_bytes = lists ? align256((size_t)gcap * sizeof(int32_t)) : 0;
+  L.pbits_bytes = push ? align256((size_t)nnz * sizeof(uint32_t)) : 0;
+  // push items of one round: kPushChunk-entry chunks of the rows of nodes of degree > t1
+  L.pq_bytes = push ? align256((size_t)(nnz / ipgc::kPushChunk + nbig + 1) * sizeof(int4)) : 0;
   L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes +
             2 * L.alist_bytes + 2 * L.flen_bytes + 2 * L.fst_bytes +
-            (filt ? 2 * L.items_bytes : 0);
+            (filt ? 2 * L.items_bytes : 0) + (push ? L.pbits_bytes + L.pq_bytes + L.a4n : 0);
   return L;
 }
 
 size_t ws_bytes_for(int32_t n, int64_t nnz, const ipgc_options& o) {
-  return ws_layout(n, nnz, effective_t1(o), effective_chunk(o), effective_filt_deg(o)).total;
+  return ws_layout(n, nnz, effective_t1(o), effective_chunk(o), effective_filt_deg(o),
+                   effective_push(o))
+      .total;
 }
 
 int ensure_ws(ipgc_ctx* ctx, int32_t n, int64_t nnz, const ipgc_options& o) {
@@ -192,7 +210,8 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.t1 = effective_t1(o);
   p.chunk = effective_chunk(o);
   p.filt_deg = effective_filt_deg(o);
-  const WsLayout L = ws_layout(n, nnz, p.t1, p.chunk, p.filt_deg);
+  const bool push = effective_push(o);
+  const WsLayout L = ws_layout(n, nnz, p.t1, p.chunk, p.filt_deg, push);
   const size_t a = L.a4n;
   char* w = ctx->ws;
   p.tent = (int32_t*)w;
@@ -228,13 +247,23 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
     w += L.fst_bytes;
     p.fdead = (int32_t*)w;
     w += L.fst_bytes;
-    p.fitems[0] = (int4*)w;
-    w += L.items_bytes;
-    p.fitems[1] = (int4*)w;
-    // hand over to filtering once |WL| <= filter_start * n
-    const double fs = o.filter_start > 0 ? (double)o.filter_start : ipgc::kDefaultFiltStart;
-    const double hw = fs * (double)n;
-    p.handoff_wl = hw >= 1.0 ? (int64_t)hw : 1;
+    if (p.filt_deg != INT32_MAX) {
+      p.fitems[0] = (int4*)w;
+      w += L.items_bytes;
+      p.fitems[1] = (int4*)w;
+      w += L.items_bytes;
+      // hand over to filtering once |WL| <= filter_start * n
+      const double fs = o.filter_start > 0 ? (double)o.filter_start : ipgc::kDefaultFiltStart;
+      const double hw = fs * (double)n;
+      p.handoff_wl = hw >= 1.0 ? (int64_t)hw : 1;
+    }
+  }
+  if (push) {
+    p.pbits = (uint32_t*)w;
+    w += L.pbits_bytes;
+    p.pq = (int4*)w;
+    w += L.pq_bytes;
+    p.pw = (int32_t*)w;
   }
   p.ctrl = ctx->d_ctrl;
   p.trace = o.trace;
@@ -320,7 +349,7 @@ int run_hostloop(ipgc_ctx* ctx, const Params& p0, int bs, int blocks, cudaStream
     }
     if (p.filt_r0 == 0 && ipgc::handoff_now(p, r, total, ctx->h_ctrl->dsum[par], ctx->h_ctrl->maxc)) {
       // hand over to neighbour filtering: list counts and states start at zero
-      const WsLayout L = ws_layout(p.n, p.nnz, p.t1, p.chunk, p.filt_deg);
+      const WsLayout L = ws_layout(p.n, p.nnz, p.t1, p.chunk, p.filt_deg, false);
       IPGC_CUDA(ctx, cudaMemsetAsync(p.flen[0], 0, 2 * L.flen_bytes + 2 * L.fst_bytes, s));
       p.filt_r0 = r;
     }
@@ -462,6 +491,9 @@ int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int3
   if (!(o.threshold_frac >= 0.0f)) return IPGC_ERR_INVALID;
   if (o.worklist != IPGC_WORKLIST_KEEP && o.worklist != IPGC_WORKLIST_REBUILD) return IPGC_ERR_INVALID;
   if (o.worklist == IPGC_WORKLIST_REBUILD && o.driver != IPGC_DRIVER_PERSISTENT)
+    return IPGC_ERR_UNSUPPORTED;
+  if (o.forbidden < IPGC_FORBIDDEN_AUTO || o.forbidden > IPGC_FORBIDDEN_PUSH) return IPGC_ERR_INVALID;
+  if (o.forbidden == IPGC_FORBIDDEN_PUSH && o.driver != IPGC_DRIVER_PERSISTENT)
     return IPGC_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard g(ctx->device);

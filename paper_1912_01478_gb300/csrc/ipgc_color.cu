@@ -38,9 +38,21 @@ namespace ipgc {
 
 template <int BS>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(const __grid_constant__ Params p) {
+  // after a pushing kernel (p.pbits set) only when that one left the colouring to this one
+  if (p.pbits && ld_cg(&p.ctrl->push_off) == 0) return;
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
   color_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// The whole colouring with forbidden-colour bitmaps (Params::pbits): a
+// separate instantiation, so the kernels that rescan rows keep their
+// register budget.
+template <int BS>
+__global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_push_kernel(const __grid_constant__ Params p) {
+  __shared__ Smem<BS> sm;
+  smem_clear<BS>(sm);
+  color_graph<BS, true>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
 }
 
 // The rounds after the hand-over to neighbour filtering (enqueued right after
@@ -63,7 +75,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) round1_kernel(const __grid
   // with t1 chosen on the device, maxdeg_kernel ran before this launch
   const int t1 = p.t1_auto ? auto_t1(p, ld_cg(&p.ctrl->maxdeg)) : p.t1;
   if (blockIdx.x == 0 && threadIdx.x == 0) p.ctrl->t1 = t1;
-  round1<BS>(p, sm, acc, Team{(int)blockIdx.x, (int)gridDim.x}, t1);
+  round1<BS>(p, sm, acc, Team{(int)blockIdx.x, (int)gridDim.x}, t1, false);
   phase_commit<BS>(p, sm, acc, 0);
   if (blockIdx.x == 0 && threadIdx.x == 0) trace_round1(p, t0);
 }
@@ -167,17 +179,20 @@ cudaError_t with_block_filt(int bs, bool filt, F f) {
 }
 
 cudaError_t occupancy_persistent(int bs, int* blocks_per_sm) {
-  // the smaller of the two kernels' occupancies
-  int a = 0, b = 0;
+  // the smallest of the kernels' occupancies
+  int a = 0, b = 0, c = 0;
   cudaError_t e = with_block(bs, [&](auto B) {
     cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &a, persistent_kernel<decltype(B)::value>, decltype(B)::value, 0);
     if (r == cudaSuccess)
       r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &b, persistent_filt_kernel<decltype(B)::value>, decltype(B)::value, 0);
+    if (r == cudaSuccess)
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &c, persistent_push_kernel<decltype(B)::value>, decltype(B)::value, 0);
     return r;
   });
-  *blocks_per_sm = a < b ? a : b;
+  *blocks_per_sm = a < b ? (a < c ? a : c) : (b < c ? b : c);
   return e;
 }
 
@@ -185,8 +200,13 @@ cudaError_t launch_persistent(const Params& p, int bs, int blocks, cudaStream_t 
   return with_block(bs, [&](auto B) {
     Params pp = p;
     void* args[] = {&pp};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)persistent_kernel<decltype(B)::value>,
-                                                dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+    cudaError_t e = cudaSuccess;
+    if (p.pbits)  // pushing; it leaves graphs without a node of degree > t1 to the next kernel
+      e = cudaLaunchCooperativeKernel((const void*)persistent_push_kernel<decltype(B)::value>,
+                                      dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+    if (e == cudaSuccess)
+      e = cudaLaunchCooperativeKernel((const void*)persistent_kernel<decltype(B)::value>,
+                                      dim3(blocks), dim3(decltype(B)::value), args, 0, s);
     if (e == cudaSuccess && p.handoff_wl > 0)
       e = cudaLaunchCooperativeKernel((const void*)persistent_filt_kernel<decltype(B)::value>,
                                       dim3(blocks), dim3(decltype(B)::value), args, 0, s);

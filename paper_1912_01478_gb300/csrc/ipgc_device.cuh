@@ -31,8 +31,11 @@ constexpr double kDefaultFiltStart = 1.0 / 32;  // hand over once |WL| <= n / 32
 constexpr int kBarGroups = 16;   // grid barrier: CTAs arrive in this many groups
 constexpr int kBarFlat = 64;     // ... when the team has more CTAs than this
 constexpr int kShrinkMin = 8;    // a shrinking team keeps at least this many CTAs
+constexpr int kShrinkMinPush = 64;  // ... with pushing
 constexpr int kStageSmall = 128; // per-warp staging of low-degree pushes
 constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
+constexpr int kPushMaxC = 32 * kGWords;  // forbidden-colour bitmaps hold colours 1..2048
+constexpr int kPushChunk = 256;  // row entries per queued push item (one warp window)
 
 // Per-colouring control block in device memory. Zeroed before every launch.
 struct Ctrl {
@@ -57,6 +60,11 @@ struct Ctrl {
   int32_t rbcnt[2];                // worklist rebuild: low-degree nodes, work items
   int32_t t1;                      // the low-degree bound in use (set before round 1)
   int32_t maxdeg;                  // largest degree (when t1 is chosen from it)
+  int32_t pqcnt;                   // push items queued by the current conflict step
+  int32_t pwcnt;                   // winners of the current conflict step still to push
+  int32_t push_off;                // the pushing kernel found no node of degree > t1 and left
+                                   // the colouring to the rescanning kernel launched after it
+  int32_t push_on;                 // forbidden-colour bitmaps in use (some degree > t1)
   // arrival counters of the grid barrier's groups, one 32-byte sector each
   uint32_t bar_grp[kBarGroups][8];
 };
@@ -113,6 +121,25 @@ struct Params {
   int32_t wl_rebuild; // topology-driven rounds keep no worklist; it is rebuilt on the way back
   int32_t t1_auto;    // choose t1 on the device: the largest degree if <= kMaxT1, else t1
   int64_t handoff_wl; // hand over when |WL| <= handoff_wl (0: never)
+  // Forbidden-colour bitmaps (pbits == nullptr: off). A node v of degree
+  // d > t1 keeps the colours of its finalised neighbours as a bitmap of
+  // ceil(min(d, kPushMaxC) / 32) words at pbits[rowptr[v]] (inside its own
+  // row range of an nnz-word buffer; bit c - 1 = colour c): every node ORs
+  // its colour into the bitmaps of its neighbours when it is committed, so
+  // the assignment step of v reads the bitmap instead of the row. The
+  // conflict step lists its winners (pw: nodes of degree <= t1; pq: the
+  // kPushChunk-entry chunks {v, chunk, gslot, #chunks} of the rows of the
+  // others), and a push phase of the whole team follows it. A node with
+  // several items also keeps the list of its lower-ID neighbours that are
+  // still active (alist/flen/fst/fdead as for neighbour filtering, lower
+  // part only; built in round 2, rewritten without finalised entries by the
+  // assignment step once a quarter of what the conflict step read was
+  // finalised), which its conflict step reads instead of the row. Used in
+  // round r while every colour committed before round r - 1 is
+  // <= kPushMaxC - 2, so every colour of round r fits the bitmaps.
+  uint32_t* pbits;
+  int4* pq;
+  int32_t* pw;
   // Optional result publication into host-mapped pinned memory (nullptr:
   // none). When a graph is done its team copies the colours to out_colors
   // and the control block to out_ctrl, then sets *out_done = 1, so the host

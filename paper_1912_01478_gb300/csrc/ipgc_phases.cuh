@@ -107,12 +107,16 @@ __device__ __forceinline__ int num_chunks(int d, int chunk) { return (d + chunk 
 
 // ---------------------------------------------------------------- round 1 --
 
+__device__ __forceinline__ void small_push(const Params& p, int s, int d, int t, int t1,
+                                           bool check_active);
+
 // Round 1: all nodes active, all tentative colours 1. v wins iff no
 // neighbour has a lower ID. Builds the worklist of round 2 (parity 0) and
 // the static work items of every high-degree node used by later topology
 // sweeps; hands out merge-state slots to nodes with several items.
-template <int BS>
-__device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, int t1) {
+template <int BS, bool PUSH = false>
+__device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, int t1,
+                       bool pushing) {
   Ctrl* c = p.ctrl;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   WarpStage ss{sm.stage_s[warp], 0};
@@ -120,10 +124,11 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, in
   for (int64_t base = (int64_t)tm.cta * BS; base < p.n; base += (int64_t)tm.ncta * BS) {
     const int v = (int)(base + threadIdx.x);
     const bool valid = v < p.n;
-    int d = 0;
+    int d = 0, s = 0;
     bool lose = false;
     if (valid) {
-      const int s = ld_ro(p.rowptr + v), e = ld_ro(p.rowptr + v + 1);
+      s = ld_ro(p.rowptr + v);
+      const int e = ld_ro(p.rowptr + v + 1);
       d = e - s;
       lose = d > 0 && ld_ro(p.col + s) < v;
       p.color[v] = lose ? 0 : 1;
@@ -151,11 +156,22 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, in
         p.done_a[gslot] = 0;
         p.done_d[gslot] = 0;
         p.flag[gslot] = 0;
+        if (PUSH && p.alist[0]) {  // lower-neighbour list state
+          p.flen[0][gslot] = make_int2(0, 0);
+          p.flen[1][gslot] = make_int2(0, 0);
+          p.fst[gslot] = 0;
+          p.fdead[gslot] = 0;
+        }
       }
     }
     items_push(st, v, nch, gslot, p.istat, &c->nistat);
     items_push(si, v, keep && lose ? nch : 0, gslot, p.items[0], &c->icnt[0]);
     if (big && lose) acc.nbig += 1;
+    if (PUSH && pushing) {  // winners: colour 1 into their neighbours' bitmaps
+      const bool win = valid && !lose;
+      small_push(p, s, win && !big ? d : 0, 1, t1, false);
+      items_push_direct(v, win && big ? num_chunks(d, kPushChunk) : 0, gslot, p.pq, &c->pqcnt);
+    }
   }
   stage_flush(ss, p.wl[0], &c->cnt[0][B_SMALL]);
   items_flush(st, p.istat, &c->nistat);
@@ -362,6 +378,94 @@ __device__ __forceinline__ void prefetch_l2(const Params& p, int64_t lo, int64_t
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p.col + a), "r"(sz) : "memory");
 }
 
+// ------------------------------------------------- forbidden-colour bitmaps --
+//
+// With pushing on (Params::pbits), a node of degree > t1 finds its colour in
+// a bitmap of its finalised neighbours' colours that those neighbours filled
+// when they were committed, instead of rescanning its row every round. The
+// colours are the same: the bitmap of v at the start of round r holds
+// exactly the colours committed to v's neighbours before round r (every
+// commit pushes before the round's last barrier; the assignment step only
+// reads). Colours above min(d, kPushMaxC) are not kept: the first free
+// colour of a node of degree d is at most d + 1, and at most maxc + 1 <=
+// kPushMaxC while pushing is on.
+
+__device__ __forceinline__ int push_words(int d) { return (min(d, kPushMaxC) + 31) >> 5; }
+
+constexpr int kPushUnroll = 8;
+
+// Colour t (just committed) into the bitmaps of the neighbours in entries
+// [lo, hi) of col that keep one (degree > t1 and >= t) and are still active
+// (check_active; round 1 pushes before colours are written and all
+// neighbours of its winners are active). One warp.
+inline __device__ __noinline__ void push_range(const Params& p, int64_t lo, int64_t hi, int t, int t1,
+                                           bool check_active) {
+  const uint64_t pol = l2_keep_policy();
+  const unsigned bit = 1u << ((t - 1) & 31);
+  const int word = (t - 1) >> 5;
+  for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
+    int u[kGather];
+    load_window(p, a, lo, hi, -1, u);
+    int sw[kGather], dw[kGather], cw[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      sw[q] = 0;
+      dw[q] = 0;
+      cw[q] = 0;
+      if (u[q] >= 0) {
+        sw[q] = ld_ro(p.rowptr + u[q]);
+        dw[q] = ld_ro(p.rowptr + u[q] + 1);
+        if (check_active) cw[q] = ld_keep(p.color + u[q], pol);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      const int d = dw[q] - sw[q];
+      if (u[q] >= 0 && d > t1 && d >= t && cw[q] == 0) atomicOr(p.pbits + sw[q] + word, bit);
+    }
+  }
+}
+
+// The same for the 32 nodes of a warp, one per lane (colour t, entries
+// [s, s + d); d = 0 for a lane that pushes nothing), their rows laid end to
+// end as in the low-degree steps.
+__device__ __forceinline__ void small_push(const Params& p, int s, int d, int t, int t1,
+                                           bool check_active) {
+  const int lane = lane_id();
+  const uint64_t pol = l2_keep_policy();
+  const SmallSeg g = small_scan(d);
+  for (int base = 0; base < g.total; base += 32 * kPushUnroll) {
+    int u[kPushUnroll], tq[kPushUnroll];
+#pragma unroll
+    for (int q = 0; q < kPushUnroll; ++q) {
+      const int e = base + q * 32 + lane;
+      const int jj = small_owner(g.off, e);
+      const int sj = __shfl_sync(FULL, s, jj);
+      const int oj = __shfl_sync(FULL, g.off, jj);
+      tq[q] = __shfl_sync(FULL, t, jj);
+      u[q] = e < g.total ? ld_ro(p.col + sj + (e - oj)) : -1;
+    }
+    int sw[kPushUnroll], dw[kPushUnroll], cw[kPushUnroll];
+#pragma unroll
+    for (int q = 0; q < kPushUnroll; ++q) {
+      sw[q] = 0;
+      dw[q] = 0;
+      cw[q] = 0;
+      if (u[q] >= 0) {
+        sw[q] = ld_ro(p.rowptr + u[q]);
+        dw[q] = ld_ro(p.rowptr + u[q] + 1);
+        if (check_active) cw[q] = ld_keep(p.color + u[q], pol);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPushUnroll; ++q) {
+      const int dd = dw[q] - sw[q];
+      if (u[q] >= 0 && dd > t1 && dd >= tq[q] && cw[q] == 0)
+        atomicOr(p.pbits + sw[q] + ((tq[q] - 1) >> 5), 1u << ((tq[q] - 1) & 31));
+    }
+  }
+}
+
 // Colours of neighbours k in [b, e) of row s, shifted by -wbase, into the
 // lane-private mask (1..32) and the warp's bitmap wb (33..lim). The next
 // window's entries are loaded while the current window's colours are
@@ -470,18 +574,31 @@ __device__ __forceinline__ void item_assign(const Params& p, unsigned* wb, int v
   }
 }
 
+// Assignment step of node v (degree d > t1, row at s) from its bitmap: the
+// first colour none of its finalised neighbours has. One warp.
+__device__ __forceinline__ void item_assign_push(const Params& p, int v, int s, int d) {
+  const int nw = push_words(d);
+  const uint32_t* b = p.pbits + s;
+  int t = first_free_64(nw, [&](int i) { return __ldcg(b + i); });
+  if (t == 0) t = 32 * nw + 1;  // colours 1..d all taken (d = 32 * nw <= kPushMaxC)
+  if (lane_id() == 0) p.tent[v] = t;
+}
+
 // Conflict step for work item (v, c); the warp that finishes v's last item
 // commits v or pushes its items to the next worklist.
 __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, int v, int s, int d,
                                             int c, int nch, int gslot, int nxt, PhaseAcc& acc,
-                                            int round, bool push = true) {
+                                            int round, bool push = true,
+                                            WarpStage* wst = nullptr) {
   const int lane = lane_id();
   const uint64_t pol = l2_keep_policy();
   const int t = ld_cg(p.tent + v);
   const int b = c * p.chunk, e = min(d, b + p.chunk);
   const int64_t lo = (int64_t)s + b, hi = (int64_t)s + e;
   bool hit = false;
-  {
+  // another item of v found a conflict already: v loses whatever this one finds
+  const bool lost = nch > 1 && ld_cg(p.flag + gslot) != 0;
+  if (!lost) {
     int64_t a = lo & ~int64_t(3);
     int u[kGather];
     load_window(p, a, lo, hi, -1, u);
@@ -526,6 +643,178 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
   }
   items_push(stage, v, (push && finisher && lose && lane == 0) ? nch : 0, gslot, p.items[nxt],
              &p.ctrl->icnt[nxt]);
+  if (finisher && lane == 0) {
+    if (lose) {
+      acc.nbig += 1;
+      acc.dsum += (unsigned long long)d;
+    } else {
+      p.color[v] = t;
+      acc.maxc = max(acc.maxc, t);
+      if (p.fin) p.fin[v] = round;
+    }
+  }
+  if (wst)  // pushing: the push phase after this step ORs t into the neighbours' bitmaps
+    items_push_direct(v, finisher && !lose && lane == 0 ? num_chunks(d, kPushChunk) : 0, gslot,
+                      p.pq, &p.ctrl->pqcnt);
+}
+
+// ------------------------------------- lower-neighbour lists (with pushing) --
+//
+// Under pushing a node with several work items (a merge-state slot) keeps
+// the list of its lower-ID neighbours that are still active, in alist[b]
+// at [rowptr[v], rowptr[v] + flen[b][gslot].x); fst[gslot]: bit 0 b, bit 1
+// "rewrite in the next assignment step", bit 2 "built". Its conflict step
+// reads the list instead of the lower part of its row: every active
+// lower-ID neighbour is on it, and the finalised ones it may still hold
+// cannot clash (tent[v] excludes their colours). The first assignment step
+// after round 1 builds it from the row; later ones rewrite it, without its
+// finalised entries, once a quarter of the entries the conflict step
+// sampled were finalised.
+
+// Entries [lo, hi) of src (the sorted row when from_col): those of ID < v
+// whose colour is 0 appended to v's list at dst[s + *len...]. One warp.
+__device__ __forceinline__ void plist_append(const Params& p, const int32_t* src, bool from_col,
+                                             int64_t lo, int64_t hi, int v, int64_t s,
+                                             int32_t* dst, int* len) {
+  const int lane = lane_id();
+  const uint64_t pol = l2_keep_policy();
+  for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
+    int u[kGather];
+    if (from_col)
+      load_window(p, a, lo, hi, -1, u);
+    else
+      load_window_rw(src, a, lo, hi, -1, u);
+    int cc[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q)
+      cc[q] = (u[q] >= 0 && u[q] < v) ? ld_keep(p.color + u[q], pol) : 1;
+    int k = 0;
+    bool above = false;
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      k += cc[q] == 0;
+      above |= u[q] >= v;
+    }
+    int x = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    const int tot = __shfl_sync(FULL, x, 31);
+    if (tot) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(len, tot);
+      int o = __shfl_sync(FULL, base, 0) + x - k;
+#pragma unroll
+      for (int q = 0; q < kGather; ++q)
+        if (cc[q] == 0) dst[s + o++] = u[q];
+    }
+    if (from_col && __any_sync(FULL, above)) break;  // sorted row: no lower ID follows
+  }
+}
+
+// Assignment step for work item c of nch of node v with a merge-state slot:
+// item 0 takes tent[v] from the bitmap; every item builds or rewrites its
+// share of the list.
+__device__ __forceinline__ void item_assign_plist(const Params& p, int v, int s, int d, int c,
+                                                  int nch, int gslot) {
+  if (c == 0) item_assign_push(p, v, s, d);
+  const int st = ld_cg(p.fst + gslot);
+  if (!(st & 4)) {  // built from row chunk c (the items of a node without a list are its row's)
+    const int64_t lo = (int64_t)s + (int64_t)c * p.chunk;
+    const int64_t hi = min((int64_t)s + d, lo + p.chunk);
+    if (lo < hi && ld_ro(p.col + lo) < v)
+      plist_append(p, p.col, true, lo, hi, v, s, p.alist[0], &p.flen[0][gslot].x);
+  } else if (st & 2) {
+    const int cur = st & 1;
+    const int L = ld_cg(&p.flen[cur][gslot].x);
+    const int64_t lo = s + (int64_t)L * c / nch, hi = s + (int64_t)L * (c + 1) / nch;
+    plist_append(p, p.alist[cur], false, lo, hi, v, s, p.alist[cur ^ 1],
+                 &p.flen[cur ^ 1][gslot].x);
+  }
+}
+
+// Conflict step for work item c of nch of node v with a merge-state slot:
+// its share of the list up to the first clash. The warp that finishes v's
+// last item commits v (queueing its row for the push phase) or pushes its
+// items for round r + 1 (chunks of the list while the next round pushes,
+// else of the row), and sets the list state. The finalised entries among
+// the first window of each item are counted in fdead, all entries of those
+// windows in done_a (idle in this mode).
+__device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& stage, int v, int s,
+                                                  int d, int c, int nch, int gslot, int nxt,
+                                                  PhaseAcc& acc, int round, bool push,
+                                                  bool lists_next) {
+  const int lane = lane_id();
+  const uint64_t pol = l2_keep_policy();
+  const int t = ld_cg(p.tent + v);
+  const int st = ld_cg(p.fst + gslot);
+  const int cur = st & 1;
+  const int nb = !(st & 4) ? 0 : ((st & 2) ? cur ^ 1 : cur);
+  const int L = ld_cg(&p.flen[nb][gslot].x);
+  const int32_t* lst = p.alist[nb];
+  const int64_t lo = s + (int64_t)L * c / nch, hi = s + (int64_t)L * (c + 1) / nch;
+  bool hit = false;
+  int dead = 0, seen = 0;
+  if (lo < hi && ld_cg(p.flag + gslot) == 0) {  // else another item found a clash already
+    int64_t a = lo & ~int64_t(3);
+    int u[kGather];
+    load_window_rw(lst, a, lo, hi, -1, u);
+    for (; a < hi; a += kWindow) {
+      int un[kGather];
+      const bool more = a + kWindow < hi;
+      if (more) load_window_rw(lst, a + kWindow, lo, hi, -1, un);  // the next window ahead
+      int tt[kGather];
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) tt[q] = u[q] >= 0 ? ld_keep(p.tent + u[q], pol) : 0;
+#pragma unroll
+      for (int q = 0; q < kGather; ++q) hit |= u[q] >= 0 && tt[q] == t;
+      if (a < lo + kWindow) {  // the item's first window samples how much of the list is finalised
+        int cc[kGather];
+#pragma unroll
+        for (int q = 0; q < kGather; ++q) cc[q] = u[q] >= 0 ? ld_keep(p.color + u[q], pol) : 0;
+#pragma unroll
+        for (int q = 0; q < kGather; ++q) {
+          seen += u[q] >= 0;
+          dead += u[q] >= 0 && cc[q] != 0;
+        }
+      }
+      if (__any_sync(FULL, hit)) break;
+      if (more) {
+#pragma unroll
+        for (int q = 0; q < kGather; ++q) u[q] = un[q];
+      }
+    }
+  }
+  hit = __any_sync(FULL, hit);
+  dead = __reduce_add_sync(FULL, dead);
+  seen = __reduce_add_sync(FULL, seen);
+  int finisher = 0, lose = 0;
+  if (lane == 0) {
+    if (hit) atomicOr(&p.flag[gslot], 1);
+    if (dead) atomicAdd(p.fdead + gslot, dead);
+    if (seen) atomicAdd(p.done_a + gslot, seen);
+    __threadfence();
+    finisher = atomicAdd(&p.done_d[gslot], 1) == nch - 1;
+    if (finisher) {
+      __threadfence();
+      lose = atomicExch(&p.flag[gslot], 0) != 0;
+      p.done_d[gslot] = 0;
+      const int D = atomicExch(p.fdead + gslot, 0);
+      const int S = atomicExch(p.done_a + gslot, 0);
+      const bool rw = D > 0 && 4 * (int64_t)D >= (int64_t)S;
+      if ((st & 6) == 6) p.flen[cur][gslot] = make_int2(0, 0);  // rewritten: the old buffer is free
+      p.fst[gslot] = nb | 4 | (rw ? 2 : 0);
+    }
+  }
+  finisher = __shfl_sync(FULL, finisher, 0);
+  lose = __shfl_sync(FULL, lose, 0);
+  const int nxt_items = lists_next ? max(1, num_chunks(L, p.chunk)) : num_chunks(d, p.chunk);
+  items_push(stage, v, (push && finisher && lose && lane == 0) ? nxt_items : 0, gslot,
+             p.items[nxt], &p.ctrl->icnt[nxt]);
+  items_push_direct(v, (finisher && !lose && lane == 0) ? num_chunks(d, kPushChunk) : 0, gslot,
+                    p.pq, &p.ctrl->pqcnt);
   if (finisher && lane == 0) {
     if (lose) {
       acc.nbig += 1;
@@ -889,6 +1178,7 @@ struct RoundView {
   int r0;      // first round of neighbour filtering (0: not started)
   int t1;      // the low-degree bound in use
   int filt;    // nodes of degree > filt_deg read filtered lists this round
+  int push;    // nodes of degree > t1 read their forbidden-colour bitmaps this round
   unsigned long long dsum;  // degree sum of the worklist
 };
 
@@ -910,6 +1200,11 @@ __device__ __forceinline__ RoundView read_round(const Params& p, int r) {
   rv.r0 = p.filt_r0 > 0 ? p.filt_r0 : ld_cg(&p.ctrl->handoff_round);
   rv.filt = p.alist[0] != nullptr && rv.r0 > 0 && r >= rv.r0 &&
             ld_cg(&p.ctrl->maxc_start[(r - 1) & 1]) <= kFiltMaxC;
+  // pushing in round r iff the colours committed before round r - 1 are
+  // <= kPushMaxC - 2: round r - 1 adds at most 1, so every tentative colour of
+  // round r is <= kPushMaxC and the bitmaps hold it
+  rv.push = p.pbits != nullptr && ld_cg(&p.ctrl->push_on) != 0 &&
+            ld_cg(&p.ctrl->maxc_start[(r - 1) & 1]) <= kPushMaxC - 2;
   return rv;
 }
 
@@ -954,6 +1249,8 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
   c->icnt[nxt] = 0;
   c->ficnt[nxt] = 0;
   c->dsum[nxt] = 0;
+  c->pqcnt = 0;
+  c->pwcnt = 0;
   c->rounds = r;
   c->maxc_start[r & 1] = rv.maxc;
   c->mode_at[r & 1] = rv.mode;
@@ -977,7 +1274,7 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
     tr.max_color = rv.maxc;
     tr.shortcut = 0;
     tr.wl_small = rv.nsmall;
-    tr.reserved = 0;
+    tr.push_ns = 0;
     tr.t_begin = gtime();
   }
   __threadfence();
@@ -993,13 +1290,21 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
 // Assignment step of work items [k = gwarp, gwarp + nwarps, ...) of a list.
 template <int BS>
 __device__ __forceinline__ void assign_items(const Params& p, Smem<BS>& sm, const int4* items,
-                                             int count, bool topo, int maxc, Team tm) {
+                                             int count, bool topo, int maxc, bool pushing,
+                                             Team tm) {
   const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   unsigned* wb = sm.wbits[warp];
-  for_items(p, items, count, topo, gwarp, nwarps, INT_MAX,
+  for_items(p, items, count, topo, gwarp, nwarps, pushing ? -1 : INT_MAX,
             [&](int v, int c, int gslot, int nch, int s, int d) {
-              item_assign(p, wb, v, s, d, c, nch, gslot, maxc);
+              if (pushing) {
+                if (gslot >= 0)
+                  item_assign_plist(p, v, s, d, c, nch, gslot);
+                else if (c == 0)
+                  item_assign_push(p, v, s, d);
+              } else {
+                item_assign(p, wb, v, s, d, c, nch, gslot, maxc);
+              }
             });
 }
 
@@ -1049,7 +1354,7 @@ __device__ __forceinline__ void assign_small_nodes(const Params& p, Smem<BS>& sm
                    [&](int v, int s, int d, int) { small_assign(p, v, s, d, wm); });
 }
 
-template <int BS, bool FILT>
+template <int BS, bool FILT, bool PUSH = false>
 __device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv, Team tm) {
   const bool topo = rv.mode == MODE_TOPO;
   const int4* items = topo ? p.istat : p.items[rv.par];
@@ -1060,7 +1365,7 @@ __device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
   if (FILT && rv.filt && (topo || rv.round == rv.r0)) {
     if (gwarp < count) assign_mixed<BS>(p, sm, items, count, rv, tm);
   } else {
-    assign_items<BS>(p, sm, items, count, topo, rv.maxc, tm);
+    assign_items<BS>(p, sm, items, count, topo, rv.maxc, PUSH && rv.push, tm);
     if (FILT && rv.filt && gwarp < rv.ficnt) assign_fitems<BS>(p, sm, rv, tm);
   }
   assign_small_nodes<BS>(p, sm, rv, tm);
@@ -1070,14 +1375,20 @@ __device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
 template <int BS>
 __device__ __forceinline__ PhaseAcc detect_items(const Params& p, ItemStage& stage,
                                                  const int4* items, int count, bool topo,
-                                                 int round, int nxt, Team tm) {
+                                                 int round, int nxt, WarpStage* wst,
+                                                 bool lists_next, Team tm) {
   const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   PhaseAcc acc;
   const bool push = !(topo && p.wl_rebuild);  // rebuild: topology sweeps keep no worklist
-  for_items(p, items, count, topo, gwarp, nwarps, INT_MAX,
+  // (with pushing, nodes with a merge-state slot read their lists, not their rows)
+  for_items(p, items, count, topo, gwarp, nwarps, wst ? p.chunk : INT_MAX,
             [&](int v, int cidx, int gslot, int nch, int s, int d) {
-              item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round, push);
+              if (wst && gslot >= 0)
+                item_detect_plist(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round, push,
+                                  lists_next);
+              else
+                item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round, push, wst);
             });
   return acc;
 }
@@ -1139,7 +1450,8 @@ __device__ __noinline__ PhaseAcc detect_fitems(const Params& p, Smem<BS>& sm, It
 
 template <int BS>
 __device__ __forceinline__ PhaseAcc detect_small_nodes(const Params& p, Smem<BS>& sm,
-                                                       const RoundView& rv, Team tm) {
+                                                       const RoundView& rv, WarpStage* wst,
+                                                       Team tm) {
   const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   const bool topo = rv.mode == MODE_TOPO;
@@ -1165,6 +1477,8 @@ __device__ __forceinline__ PhaseAcc detect_small_nodes(const Params& p, Smem<BS>
                         if (p.fin) p.fin[v] = rv.round;
                       }
                     }
+                    if (wst)  // pushing: winners for the push phase
+                      stage_push(*wst, kStageSmall, v >= 0 && !lose, v, p.pw, &c->pwcnt);
                   });
   stage_flush(sg, p.wl[nxt], &c->cnt[nxt][B_SMALL]);
   return acc;
@@ -1216,7 +1530,7 @@ __device__ __noinline__ void rebuild_worklists(const Params& p, Smem<BS>& sm, co
   items_flush(st, p.items[rv.par], &c->rbcnt[1]);
 }
 
-template <int BS, bool FILT>
+template <int BS, bool FILT, bool PUSH = false>
 __device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv, PhaseAcc& acc,
                              Team tm) {
   const int warp = threadIdx.x >> 5;
@@ -1225,16 +1539,56 @@ __device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
   const int4* items = topo ? p.istat : p.items[rv.par];
   const int count = topo ? rv.nistat : rv.icnt;
   ItemStage stage{sm.stage_i[warp], 0};
+  // with pushing, the winners are staged in the (then idle) filtered-item buffer
+  static_assert(sizeof(sm.stage_t[0]) >= kStageSmall * sizeof(int32_t), "winner stage");
+  WarpStage wst_buf{reinterpret_cast<int32_t*>(sm.stage_t[warp]), 0};
+  WarpStage* wst = PUSH && rv.push ? &wst_buf : nullptr;
   const int gwarp = tm.cta * (BS / 32) + warp;
   if (FILT && rv.filt && (topo || rv.round == rv.r0)) {
     if (gwarp < count) acc_merge(acc, detect_mixed<BS>(p, sm, stage, items, count, rv, tm));
   } else {
-    acc_merge(acc, detect_items<BS>(p, stage, items, count, topo, rv.round, nxt, tm));
+    acc_merge(acc, detect_items<BS>(p, stage, items, count, topo, rv.round, nxt, wst,
+                                    rv.maxc <= kPushMaxC - 2, tm));
     if (FILT && rv.filt && gwarp < rv.ficnt)
       acc_merge(acc, detect_fitems<BS>(p, sm, stage, rv, tm));
   }
   items_flush(stage, p.items[nxt], &p.ctrl->icnt[nxt]);
-  acc_merge(acc, detect_small_nodes<BS>(p, sm, rv, tm));
+  acc_merge(acc, detect_small_nodes<BS>(p, sm, rv, wst, tm));
+  if (wst) stage_flush(*wst, p.pw, &p.ctrl->pwcnt);
+}
+
+// The push phase that follows a conflict step (or round 1) with pushing:
+// the colours of the nodes committed in it into their active neighbours'
+// bitmaps. Work units: the queued kPushChunk-entry chunks of the rows of
+// winners of degree > t1 (one warp each), then the listed low-degree
+// winners 32 at a time (their rows laid end to end, at most 32 * t1
+// entries). A team barrier follows.
+template <int BS>
+__device__ __noinline__ void push_phase(const Params& p, int nq, int nw, int t1, Team tm) {
+  const int gwarp = tm.cta * (BS / 32) + (threadIdx.x >> 5), nwarps = tm.ncta * (BS / 32);
+  const int lane = lane_id();
+  const int units = nq + (nw + 31) / 32;
+  for (int k = gwarp; k < units; k += nwarps) {
+    if (k < nq) {
+      const int4 it = ld_cg4(p.pq + k);
+      const int v = it.x;
+      const int s = ld_ro(p.rowptr + v), e = ld_ro(p.rowptr + v + 1);
+      const int t = ld_cg(p.color + v);
+      const int64_t lo = (int64_t)s + (int64_t)it.y * kPushChunk;
+      const int64_t hi = min((int64_t)e, lo + kPushChunk);
+      push_range(p, lo, hi, t, t1, true);
+    } else {
+      const int i = (k - nq) * 32 + lane;
+      int s = 0, d = 0, t = 1;
+      if (i < nw) {
+        const int v = ld_cg(p.pw + i);
+        s = ld_ro(p.rowptr + v);
+        d = ld_ro(p.rowptr + v + 1) - s;
+        t = ld_cg(p.color + v);
+      }
+      small_push(p, s, d, t, t1, true);
+    }
+  }
 }
 
 __device__ __forceinline__ void trace_round1(const Params& p, uint64_t t0) {
@@ -1253,7 +1607,7 @@ __device__ __forceinline__ void trace_round1(const Params& p, uint64_t t0) {
     tr.max_color = 0;
     tr.shortcut = 1;
     tr.wl_small = 0;
-    tr.reserved = 0;
+    tr.push_ns = 0;
     tr.t_begin = t0;
     tr.t_assign = t0;
     tr.t_detect = t1;
@@ -1310,12 +1664,19 @@ __device__ __forceinline__ int auto_t1(const Params& p, int maxdeg) {
   return maxdeg <= kMaxT1 ? (maxdeg > 0 ? maxdeg : 1) : p.t1;
 }
 
-// The largest degree of the graph into ctrl->maxdeg, then a team barrier.
+// The largest degree of the graph into ctrl->maxdeg and, with pushing, the
+// forbidden-colour bitmaps of every node that may keep one (degree > the
+// given t1, which the t1 in use never undercuts where such nodes exist)
+// cleared; then a team barrier.
 template <int BS>
-__device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm) {
+__device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm, bool zero) {
   int m = 0;
-  for (int64_t v = (int64_t)tm.cta * BS + threadIdx.x; v < p.n; v += (int64_t)tm.ncta * BS)
-    m = max(m, ld_ro(p.rowptr + v + 1) - ld_ro(p.rowptr + v));
+  for (int64_t v = (int64_t)tm.cta * BS + threadIdx.x; v < p.n; v += (int64_t)tm.ncta * BS) {
+    const int s = ld_ro(p.rowptr + v), d = ld_ro(p.rowptr + v + 1) - s;
+    m = max(m, d);
+    if (zero && d > p.t1)
+      for (int i = 0, nw = push_words(d); i < nw; ++i) p.pbits[s + i] = 0u;
+  }
   m = block_max<BS>(sm, m);
   if (threadIdx.x == 0 && m > 0) atomicMax(&p.ctrl->maxdeg, m);
   return team_barrier(p.ctrl, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
@@ -1325,7 +1686,7 @@ __device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm) {
 // by the team's bounded barrier, until the worklist is empty. Without FILT
 // the loop stops early at the hand-over round (handoff_now), which it
 // records for continue_graph.
-template <int BS, bool FILT>
+template <int BS, bool FILT, bool PUSH = false>
 __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) {
   Ctrl* c = p.ctrl;
   const bool lead = tm.cta == 0 && threadIdx.x == 0;
@@ -1337,7 +1698,7 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       if (lead) atomicCAS(&c->status, 0, IPGC_ERR_NO_CONVERGE);
       break;
     }
-    if (!FILT && handoff_now(p, r, total, rv.dsum, rv.maxc)) {
+    if (!FILT && !PUSH && handoff_now(p, r, total, rv.dsum, rv.maxc)) {
       if (lead) c->handoff_round = r;
       break;
     }
@@ -1356,22 +1717,34 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       // (the worklist only shrinks)
       const int64_t units = (int64_t)rv.icnt + (FILT ? rv.ficnt : 0) + ((int64_t)rv.nsmall + 31) / 32;
       const int64_t want = (units + (BS / 32) - 1) / (BS / 32);
-      const int k = (int)(want > kShrinkMin ? want : kShrinkMin);
+      // (with pushing a high-degree winner's whole row is pushed after the
+      // conflict step, one warp per kPushChunk entries: keep more CTAs)
+      const int kmin = PUSH && rv.push ? kShrinkMinPush : kShrinkMin;
+      const int k = (int)(want > kmin ? want : kmin);
       if (4 * k <= tm.ncta) {
         if (tm.cta >= k) break;
         tm.ncta = k;
       }
     }
     round_begin(p, rv, r, total, tm);
-    assign_phase<BS, FILT>(p, sm, rv, tm);
+    assign_phase<BS, FILT, PUSH>(p, sm, rv, tm);
     if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
     if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_assign = gtime();
     {
       PhaseAcc acc;
-      detect_phase<BS, FILT>(p, sm, rv, acc, tm);
+      detect_phase<BS, FILT, PUSH>(p, sm, rv, acc, tm);
       phase_commit<BS>(p, sm, acc, rv.par ^ 1);
     }
     if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+    if (PUSH && rv.push) {
+      const int q = ld_cg(&c->pqcnt), w = ld_cg(&c->pwcnt);
+      if (q > 0 || w > 0) {
+        const uint64_t tp = lead && p.trace && r <= p.trace_cap ? gtime() : 0;
+        push_phase<BS>(p, q, w, rv.t1, tm);
+        if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+        if (tp) p.trace[r - 1].push_ns = (int32_t)(gtime() - tp);
+      }
+    }
     if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_detect = gtime();
   }
 }
@@ -1380,29 +1753,47 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
 // single-graph kernel, a few CTAs or one CTA for a graph of a batch). With
 // neighbour filtering enabled it may stop at the hand-over round, and
 // continue_graph (a second launch) finishes it.
-template <int BS>
+template <int BS, bool PUSH = false>
 __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   Ctrl* c = p.ctrl;
   const bool lead = tm.cta == 0 && threadIdx.x == 0;
   const uint64_t t0 = gtime();
-  if (lead) c->t_start = t0;
+  if (lead && c->t_start == 0) c->t_start = t0;  // (a pushing kernel before this one may have set it)
   int t1 = p.t1;
-  if (p.t1_auto) {  // one pass over the row offsets: the largest degree decides t1
-    if (!team_max_degree<BS>(p, sm, tm)) {
+  bool pushing = false;
+  if (p.t1_auto || PUSH) {  // one pass over the row offsets: the largest degree decides t1
+    if (!team_max_degree<BS>(p, sm, tm, PUSH && p.pbits != nullptr)) {
       if (lead) c->t_end = gtime();
       return;
     }
-    t1 = auto_t1(p, ld_cg(&c->maxdeg));
+    const int md = ld_cg(&c->maxdeg);
+    if (p.t1_auto) t1 = auto_t1(p, md);
+    pushing = PUSH && p.pbits != nullptr && md > t1;  // some node keeps a bitmap
   }
-  if (lead) c->t1 = t1;
+  if (PUSH && !pushing) {  // every node on the low-degree path: nothing to push
+    if (lead) c->push_off = 1;
+    return;
+  }
+  if (lead) {
+    c->t1 = t1;
+    c->push_on = pushing ? 1 : 0;
+  }
   {
     PhaseAcc acc;
-    round1<BS>(p, sm, acc, tm, t1);
+    round1<BS, PUSH>(p, sm, acc, tm, t1, pushing);
     phase_commit<BS>(p, sm, acc, 0);
   }
-  if (team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) {
+  bool ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
+  if (PUSH && ok && pushing) {
+    const int q = ld_cg(&c->pqcnt);
+    if (q > 0) {
+      push_phase<BS>(p, q, 0, t1, tm);
+      ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
+    }
+  }
+  if (ok) {
     if (lead) trace_round1(p, t0);
-    run_rounds<BS, false>(p, sm, tm, 2);
+    run_rounds<BS, false, PUSH>(p, sm, tm, 2);
   }
   if (lead) c->t_end = gtime();
   if (p.out_done) publish_result<BS>(p, tm);

@@ -36,6 +36,8 @@ MODE_THRESHOLD, MODE_TOPO, MODE_DATA, MODE_LEARNED = 0, 1, 2, 3
 DRIVER_PERSISTENT, DRIVER_HOSTLOOP = 0, 1
 PUSH_WL, PUSH_NOWL, PUSH_HYBRID = 0, 1, 2
 WORKLIST_KEEP, WORKLIST_REBUILD = 0, 1
+FORBIDDEN_AUTO, FORBIDDEN_RESCAN, FORBIDDEN_PUSH = 0, 1, 2
+FORBIDDEN = {"auto": FORBIDDEN_AUTO, "rescan": FORBIDDEN_RESCAN, "push": FORBIDDEN_PUSH}
 MODES = {"threshold": MODE_THRESHOLD, "topo": MODE_TOPO, "data": MODE_DATA, "learned": MODE_LEARNED}
 DRIVERS = {"persistent": DRIVER_PERSISTENT, "hostloop": DRIVER_HOSTLOOP}
 
@@ -65,7 +67,7 @@ class TraceRec(ctypes.Structure):
         ("max_color", ctypes.c_int32),
         ("shortcut", ctypes.c_int32),
         ("wl_small", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("push_ns", ctypes.c_int32),
         ("t_begin", ctypes.c_uint64),
         ("t_assign", ctypes.c_uint64),
         ("t_detect", ctypes.c_uint64),
@@ -81,7 +83,7 @@ TRACE_DTYPE = np.dtype(
         ("max_color", np.int32),
         ("shortcut", np.int32),
         ("wl_small", np.int32),
-        ("reserved", np.int32),
+        ("push_ns", np.int32),
         ("t_begin", np.uint64),
         ("t_assign", np.uint64),
         ("t_detect", np.uint64),
@@ -110,6 +112,7 @@ class Options(ctypes.Structure):
         ("filter_degree", ctypes.c_int32),
         ("filter_start", ctypes.c_float),
         ("worklist", ctypes.c_int32),
+        ("forbidden", ctypes.c_int32),
     ]
 
 
@@ -185,6 +188,7 @@ class ColorOptions:
     filter_degree: int = 0  # 0: library default; < 0: neighbour filtering off
     filter_start: float = 0.0  # 0: library default
     worklist: str = "keep"  # "keep" (the paper's hybrid) or "rebuild" (discard and rebuild)
+    forbidden: str = "auto"  # "auto", "rescan" (reread rows every round) or "push" (bitmaps)
 
     def to_c(self, trace_ptr: int = 0, trace_cap: int = 0, fin_ptr: int = 0) -> Options:
         o = Options()
@@ -205,6 +209,7 @@ class ColorOptions:
         o.filter_degree = self.filter_degree
         o.filter_start = self.filter_start
         o.worklist = {"keep": WORKLIST_KEEP, "rebuild": WORKLIST_REBUILD}[self.worklist]
+        o.forbidden = FORBIDDEN[self.forbidden]
         return o
 
 

@@ -160,9 +160,11 @@ def _round_times(tr):
     return (tr["t_detect"].astype(np.int64) - tr["t_begin"].astype(np.int64)).astype(np.float64)
 
 
-def collect(ctx: "ipgc.Context", graphs, reps: int = 3, threshold_frac: float = 0.6) -> Traces:
+def collect(ctx: "ipgc.Context", graphs, reps: int = 3, threshold_frac: float = 0.6,
+            forbidden: str = "rescan") -> Traces:
     """Forced-mode traces of every (rowptr, col) graph: the median of `reps`
-    runs per mode and round."""
+    runs per mode and round, by default of the paper's loop (rows rescanned
+    every round, which the byte model BYTES_KAPPA describes)."""
     import torch
 
     xs, tt, td, thr, gi, ns, ws = [], [], [], [], [], [], []
@@ -177,7 +179,8 @@ def collect(ctx: "ipgc.Context", graphs, reps: int = 3, threshold_frac: float = 
             runs = []
             for _ in range(reps + 1):
                 trb = ipgc.trace_buffer(n + 2)
-                _, st = ctx.color(drp, dcl, out, ipgc.ColorOptions(mode=mode, validate=False),
+                _, st = ctx.color(drp, dcl, out,
+                                  ipgc.ColorOptions(mode=mode, validate=False, forbidden=forbidden),
                                   trace=trb)
                 runs.append(_round_times(ipgc.read_trace(trb, st.rounds)))
             times[mode] = np.median(np.stack(runs[1:]), axis=0)  # first run warms up

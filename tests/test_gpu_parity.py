@@ -154,7 +154,8 @@ def test_bucket_thresholds(ctx, t1, chunk):
     rp, cl = graphgen.rmat(13, 16, seed=11)
     ref = oracle.color(rp, cl)
     for mode in ("threshold", "topo", "data"):
-        assert_parity(ctx, rp, cl, ref, mode=mode, t1=t1, chunk=chunk)
+        for forbidden in ("auto", "rescan"):  # (auto: bitmaps with the persistent driver)
+            assert_parity(ctx, rp, cl, ref, mode=mode, t1=t1, chunk=chunk, forbidden=forbidden)
 
 
 @pytest.mark.parametrize("fdeg,t1,chunk,start", [(-1, 0, 0, 0.0), (1, 1, 32, 1.0), (24, 24, 64, 0.05),
@@ -169,7 +170,7 @@ def test_neighbour_filtering(ctx, fdeg, t1, chunk, start):
     ref = oracle.color(rp, cl)
     for mode, driver in MODES:
         assert_parity(ctx, rp, cl, ref, mode=mode, driver=driver, filter_degree=fdeg, t1=t1,
-                      chunk=chunk, filter_start=start)
+                      chunk=chunk, filter_start=start, forbidden="rescan")
 
 
 def complete(n):
@@ -186,7 +187,7 @@ def test_filtering_hands_over_beyond_the_bitmap(ctx, n):
     for mode, driver, chunk in (("data", "persistent", 0), ("topo", "persistent", 512),
                                 ("threshold", "hostloop", 256)):
         got, st = gpu_color(ctx, rp, cl, mode=mode, driver=driver, chunk=chunk, filter_degree=64,
-                            filter_start=1.0)
+                            filter_start=1.0, forbidden="rescan")
         assert st.error == 0
         assert np.array_equal(got, np.arange(1, n + 1)), (mode, driver)
         assert st.rounds == n and st.num_colors == n
@@ -208,7 +209,10 @@ def test_grid_shapes(ctx, bps):
 def test_rmat_medium(ctx, mode, driver):
     # RMAT scale 16 (65,536 nodes), edge factor 16, permuted IDs
     rp, cl = graphgen.rmat(16, 16, seed=2)
-    assert_parity(ctx, rp, cl, mode=mode, driver=driver)
+    ref = oracle.color(rp, cl)
+    assert_parity(ctx, rp, cl, ref, mode=mode, driver=driver)
+    if driver == "persistent":  # the default there pushes colours; rescanning rows as well
+        assert_parity(ctx, rp, cl, ref, mode=mode, driver=driver, forbidden="rescan")
 
 
 @pytest.mark.parametrize("mode", ["threshold", "data", "topo"])
@@ -362,7 +366,8 @@ def test_full_size_workloads(ctx, name):
     assert tr["wl_size"].tolist() == exp["wl_sizes"]
     assert tr["deg_sum"].tolist() == exp["deg_sums"]
     # the same through the host loop driver and forced modes
-    for kw in (dict(mode="data"), dict(mode="topo"), dict(driver="hostloop")):
+    for kw in (dict(mode="data"), dict(mode="topo"), dict(driver="hostloop"),
+               dict(forbidden="rescan")):
         got2, st2 = gpu_color(ctx, rp, cl, validate=False, **kw)
         assert np.array_equal(got2, got) and st2.rounds == st.rounds
 

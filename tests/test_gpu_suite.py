@@ -1,6 +1,7 @@
 """The stand-ins for the paper's ten graphs (Table I shapes), small
 versions: Plain (data-driven), Hybrid and Hybrid with neighbour filtering
-colour each exactly as the CPU oracle does."""
+(rescanning rows), Hybrid with forbidden-colour bitmaps (the default) and
+the worklist rebuild colour each exactly as the CPU oracle does."""
 import numpy as np
 import pytest
 
@@ -30,8 +31,10 @@ def test_suite_graph_matches_oracle(ctx, name):
     rp, cl = graphgen.suite_graph(name, SCALE.get(name, 0.02))
     ref = oracle.color(rp, cl, trace=False)
     drp, dcl = torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda()
-    for kw in (dict(mode="data", filter_degree=-1), dict(filter_degree=-1),
-               dict(filter_start=1.0, filter_degree=32, chunk=32), dict(worklist="rebuild")):
+    R = "rescan"
+    for kw in (dict(mode="data", filter_degree=-1, forbidden=R), dict(filter_degree=-1, forbidden=R),
+               dict(filter_start=1.0, filter_degree=32, chunk=32, forbidden=R), dict(),
+               dict(mode="data", t1=16, chunk=32), dict(worklist="rebuild")):
         colors, st = ctx.color(drp, dcl, options=ipgc.ColorOptions(**kw))
         assert np.array_equal(colors.cpu().numpy(), ref.colors), (name, kw)
         assert st.rounds == ref.rounds and st.num_colors == ref.num_colors
