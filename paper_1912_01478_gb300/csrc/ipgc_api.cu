@@ -120,7 +120,7 @@ int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
 //   With pushing (IPGC_FORBIDDEN_PUSH), the list arrays of filtering (lower
 //   parts only, no filtered items) and at the end the forbidden-colour
 //   bitmaps [nnz] words (a node's bitmap inside its own row range), the push
-//   queue [item_cap] and the winners list [n].
+//   queue and the winners list [n].
 struct WsLayout {
   size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, fst_bytes, pbits_bytes,
       pq_bytes, total;

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) assign_kernel(const __grid
   // the previous round ended when this launch began
   if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace && r - 1 <= p.trace_cap)
     p.trace[r - 2].t_detect = gtime();
-  RoundView rv = read_round(p, r);
+  RoundView rv = read_round<BS>(p, r, sm);
   rv.mode = mode;
   const int64_t total = (int64_t)rv.nsmall + rv.nbig;
   const Team tm{(int)blockIdx.x, (int)gridDim.x};
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) detect_kernel(const __grid
   smem_clear<BS>(sm);
   if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace && r <= p.trace_cap)
     p.trace[r - 1].t_assign = gtime();
-  RoundView rv = read_round(p, r);
+  RoundView rv = read_round<BS>(p, r, sm);
   rv.mode = mode;
   PhaseAcc acc;
   detect_phase<BS, FILT>(p, sm, rv, acc, Team{(int)blockIdx.x, (int)gridDim.x});

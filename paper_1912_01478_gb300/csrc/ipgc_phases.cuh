@@ -30,6 +30,7 @@ struct Smem {
   int mode_b;  // broadcast of the round's mode (learned policy)
   unsigned red2[W];
   unsigned red3[W];
+  int rvb[16];  // round state read from the control block once per CTA
 };
 
 template <int BS>
@@ -394,41 +395,60 @@ __device__ __forceinline__ int push_words(int d) { return (min(d, kPushMaxC) + 3
 
 constexpr int kPushUnroll = 8;
 
-// Colour t (just committed) into the bitmaps of the neighbours in entries
-// [lo, hi) of col that keep one (degree > t1 and >= t) and are still active
-// (check_active; round 1 pushes before colours are written and all
-// neighbours of its winners are active). One warp.
-inline __device__ __noinline__ void push_range(const Params& p, int64_t lo, int64_t hi, int t, int t1,
-                                           bool check_active) {
-  const uint64_t pol = l2_keep_policy();
+// OR `bit` into bitmap word *w unless the word, as this SM's L1 may hold it,
+// has the bit already. Bitmaps only gain bits during a colouring, and none
+// is read through L1 before it is cleared, so a cached copy holds a subset
+// of the word's bits: a stale copy costs a redundant atomic, never a missed
+// bit. A high-degree node receives one push per committed neighbour, most
+// of them for the few low colours of one word; the check keeps those off
+// the L2 atomic unit of that word.
+__device__ __forceinline__ void push_bit(uint32_t* w, unsigned bit) {
+  if ((__ldca(w) & bit) == 0) atomicOr(w, bit);
+}
+
+// Colour t into the bitmap of neighbour u, whose row starts at s and has d
+// entries (colours above d never decide u's first free colour).
+__device__ __forceinline__ void push_to(const Params& p, int s, int d, int t) {
+  if (d < t) return;
+  uint32_t* w = p.pbits + s + ((t - 1) >> 5);
   const unsigned bit = 1u << ((t - 1) & 31);
-  const int word = (t - 1) >> 5;
+  if (d > kDefaultChunk)  // many pushes reach a high-degree node
+    push_bit(w, bit);
+  else
+    atomicOr(w, bit);
+}
+
+
+// Colour t (just committed) into the bitmaps of the neighbours in entries
+// [lo, hi) of col that keep one (degree > t1) and are still active. One warp.
+inline __device__ __noinline__ void push_range(const Params& p, int64_t lo, int64_t hi, int t,
+                                               int t1) {
+  const uint64_t pol = l2_keep_policy();
   for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
     int u[kGather];
     load_window(p, a, lo, hi, -1, u);
-    int sw[kGather], dw[kGather], cw[kGather];
+    int sw[kGather], ew[kGather], cw[kGather];
 #pragma unroll
     for (int q = 0; q < kGather; ++q) {
       sw[q] = 0;
-      dw[q] = 0;
-      cw[q] = 0;
-      if (u[q] >= 0) {
+      ew[q] = 0;
+      cw[q] = 1;
+      if (u[q] >= 0) {  // three independent gathers: the push phase is latency-bound
         sw[q] = ld_ro(p.rowptr + u[q]);
-        dw[q] = ld_ro(p.rowptr + u[q] + 1);
-        if (check_active) cw[q] = ld_keep(p.color + u[q], pol);
+        ew[q] = ld_ro(p.rowptr + u[q] + 1);
+        cw[q] = ld_keep(p.color + u[q], pol);
       }
     }
 #pragma unroll
-    for (int q = 0; q < kGather; ++q) {
-      const int d = dw[q] - sw[q];
-      if (u[q] >= 0 && d > t1 && d >= t && cw[q] == 0) atomicOr(p.pbits + sw[q] + word, bit);
-    }
+    for (int q = 0; q < kGather; ++q)
+      if (cw[q] == 0 && ew[q] - sw[q] > t1) push_to(p, sw[q], ew[q] - sw[q], t);
   }
 }
 
 // The same for the 32 nodes of a warp, one per lane (colour t, entries
 // [s, s + d); d = 0 for a lane that pushes nothing), their rows laid end to
-// end as in the low-degree steps.
+// end as in the low-degree steps. In round 1 (check_active false) colours are
+// being written while it pushes, and every neighbour of a winner is active.
 __device__ __forceinline__ void small_push(const Params& p, int s, int d, int t, int t1,
                                            bool check_active) {
   const int lane = lane_id();
@@ -445,24 +465,21 @@ __device__ __forceinline__ void small_push(const Params& p, int s, int d, int t,
       tq[q] = __shfl_sync(FULL, t, jj);
       u[q] = e < g.total ? ld_ro(p.col + sj + (e - oj)) : -1;
     }
-    int sw[kPushUnroll], dw[kPushUnroll], cw[kPushUnroll];
+    int sw[kPushUnroll], ew[kPushUnroll], cw[kPushUnroll];
 #pragma unroll
     for (int q = 0; q < kPushUnroll; ++q) {
       sw[q] = 0;
-      dw[q] = 0;
-      cw[q] = 0;
+      ew[q] = 0;
+      cw[q] = 1;
       if (u[q] >= 0) {
         sw[q] = ld_ro(p.rowptr + u[q]);
-        dw[q] = ld_ro(p.rowptr + u[q] + 1);
-        if (check_active) cw[q] = ld_keep(p.color + u[q], pol);
+        ew[q] = ld_ro(p.rowptr + u[q] + 1);
+        cw[q] = check_active ? ld_keep(p.color + u[q], pol) : 0;
       }
     }
 #pragma unroll
-    for (int q = 0; q < kPushUnroll; ++q) {
-      const int dd = dw[q] - sw[q];
-      if (u[q] >= 0 && dd > t1 && dd >= tq[q] && cw[q] == 0)
-        atomicOr(p.pbits + sw[q] + ((tq[q] - 1) >> 5), 1u << ((tq[q] - 1) & 31));
-    }
+    for (int q = 0; q < kPushUnroll; ++q)
+      if (cw[q] == 0 && ew[q] - sw[q] > t1) push_to(p, sw[q], ew[q] - sw[q], tq[q]);
   }
 }
 
@@ -1182,30 +1199,55 @@ struct RoundView {
   unsigned long long dsum;  // degree sum of the worklist
 };
 
-__device__ __forceinline__ RoundView read_round(const Params& p, int r) {
+// The state of round r, read from the control block by warp 0 (one field
+// per lane) into shared memory and handed to every thread of the CTA: all
+// warps of a large team loading the same few lines at once would queue at
+// one L2 slice after every barrier. Called by every thread of the CTA.
+template <int BS>
+__device__ __forceinline__ RoundView read_round(const Params& p, int r, Smem<BS>& sm) {
+  const int par = r & 1;
+  if (threadIdx.x < 32) {
+    const Ctrl* c = p.ctrl;
+    const int32_t* dsum = reinterpret_cast<const int32_t*>(&c->dsum[par]);
+    const int32_t* src[12] = {&c->cnt[par][B_SMALL], &c->cnt[par][B_BIG], &c->icnt[par], &c->nistat,
+                              &c->ficnt[par],        &c->t1,             &c->maxc,       dsum,
+                              dsum + 1,              &c->handoff_round,  &c->maxc_start[(r - 1) & 1],
+                              &c->push_on};
+    const int lane = lane_id();
+    if (lane < 12) sm.rvb[lane] = ld_cg(src[lane]);
+  }
+  __syncthreads();
   RoundView rv;
   rv.round = r;
-  rv.par = r & 1;
-  rv.nsmall = ld_cg(&p.ctrl->cnt[rv.par][B_SMALL]);
-  rv.nbig = ld_cg(&p.ctrl->cnt[rv.par][B_BIG]);
-  rv.icnt = ld_cg(&p.ctrl->icnt[rv.par]);
-  rv.nistat = ld_cg(&p.ctrl->nistat);
-  rv.ficnt = ld_cg(&p.ctrl->ficnt[rv.par]);
-  rv.t1 = ld_cg(&p.ctrl->t1);
-  rv.maxc = ld_cg(&p.ctrl->maxc);
-  rv.dsum = __ldcg(&p.ctrl->dsum[rv.par]);
+  rv.par = par;
+  rv.nsmall = sm.rvb[0];
+  rv.nbig = sm.rvb[1];
+  rv.icnt = sm.rvb[2];
+  rv.nistat = sm.rvb[3];
+  rv.ficnt = sm.rvb[4];
+  rv.t1 = sm.rvb[5];
+  rv.maxc = sm.rvb[6];
+  rv.dsum = (unsigned long long)(uint32_t)sm.rvb[7] | ((unsigned long long)(uint32_t)sm.rvb[8] << 32);
   rv.mode = MODE_DATA;
+  const int maxc_prev = sm.rvb[10];
   // filtering in round r >= r0 iff the colours committed before round r - 1
   // fit the bitmap with room for round r - 1's (a round adds at most 1 to maxc)
-  rv.r0 = p.filt_r0 > 0 ? p.filt_r0 : ld_cg(&p.ctrl->handoff_round);
-  rv.filt = p.alist[0] != nullptr && rv.r0 > 0 && r >= rv.r0 &&
-            ld_cg(&p.ctrl->maxc_start[(r - 1) & 1]) <= kFiltMaxC;
+  rv.r0 = p.filt_r0 > 0 ? p.filt_r0 : sm.rvb[9];
+  rv.filt = p.alist[0] != nullptr && rv.r0 > 0 && r >= rv.r0 && maxc_prev <= kFiltMaxC;
   // pushing in round r iff the colours committed before round r - 1 are
   // <= kPushMaxC - 2: round r - 1 adds at most 1, so every tentative colour of
   // round r is <= kPushMaxC and the bitmaps hold it
-  rv.push = p.pbits != nullptr && ld_cg(&p.ctrl->push_on) != 0 &&
-            ld_cg(&p.ctrl->maxc_start[(r - 1) & 1]) <= kPushMaxC - 2;
+  rv.push = p.pbits != nullptr && sm.rvb[11] != 0 && maxc_prev <= kPushMaxC - 2;
   return rv;
+}
+
+// One control-block word for every thread of the CTA (read by thread 0).
+template <int BS>
+__device__ __forceinline__ int read_shared_word(const int32_t* w, Smem<BS>& sm) {
+  __syncthreads();  // earlier readers of the slot are done
+  if (threadIdx.x == 0) sm.rvb[15] = ld_cg(w);
+  __syncthreads();
+  return sm.rvb[15];
 }
 
 __device__ __forceinline__ int decide_mode(const Params& p, int64_t total) {
@@ -1576,7 +1618,7 @@ __device__ __noinline__ void push_phase(const Params& p, int nq, int nw, int t1,
       const int t = ld_cg(p.color + v);
       const int64_t lo = (int64_t)s + (int64_t)it.y * kPushChunk;
       const int64_t hi = min((int64_t)e, lo + kPushChunk);
-      push_range(p, lo, hi, t, t1, true);
+      push_range(p, lo, hi, t, t1);
     } else {
       const int i = (k - nq) * 32 + lane;
       int s = 0, d = 0, t = 1;
@@ -1691,7 +1733,7 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
   Ctrl* c = p.ctrl;
   const bool lead = tm.cta == 0 && threadIdx.x == 0;
   for (int r = r_start;; ++r) {
-    RoundView rv = read_round(p, r);
+    RoundView rv = read_round<BS>(p, r, sm);
     const int64_t total = (int64_t)rv.nsmall + rv.nbig;
     if (total == 0) break;
     if (r > p.max_rounds) {
@@ -1737,7 +1779,13 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
     }
     if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
     if (PUSH && rv.push) {
-      const int q = ld_cg(&c->pqcnt), w = ld_cg(&c->pwcnt);
+      __syncthreads();  // the previous readers of the slots are done
+      if (threadIdx.x == 0) {
+        sm.rvb[12] = ld_cg(&c->pqcnt);
+        sm.rvb[13] = ld_cg(&c->pwcnt);
+      }
+      __syncthreads();
+      const int q = sm.rvb[12], w = sm.rvb[13];
       if (q > 0 || w > 0) {
         const uint64_t tp = lead && p.trace && r <= p.trace_cap ? gtime() : 0;
         push_phase<BS>(p, q, w, rv.t1, tm);
@@ -1785,7 +1833,7 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   }
   bool ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
   if (PUSH && ok && pushing) {
-    const int q = ld_cg(&c->pqcnt);
+    const int q = read_shared_word<BS>(&c->pqcnt, sm);
     if (q > 0) {
       push_phase<BS>(p, q, 0, t1, tm);
       ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
