@@ -7,13 +7,14 @@ persistent driver) of the RMAT scale-22, edge-factor-16 graph (a, b, c, d =
 second of device time (edges/s), inputs resident in HBM.
 
 Also reported:
-  roofline      algorithmic bytes of one colouring / its average duration
-                (CUDA events on the launch stream around the call, which is
-                two launches: the rounds before the hand-over to neighbour
-                filtering and the rounds from it on), against the measured
-                HBM copy peak; per-kernel bytes and device times from the
-                round trace; DRAM traffic from the committed ncu summary when
-                it was taken on the current kernel sources;
+  roofline      algorithmic bytes of one colouring (the paper's loop, which
+                rescans the active nodes' rows every round) / its average
+                duration (CUDA events on the launch stream around the call:
+                the pushing kernel, then the rescanning kernel, which returns
+                at once when the first one coloured the graph), against the
+                measured HBM copy peak; per-kernel bytes and device times from
+                the round trace; DRAM traffic from the committed ncu summary
+                when it was taken on the current kernel sources;
   e2e           the same metric through ipgc_color_host (host buffers, the
                 copies inside the timed region);
   cpu_baseline  the CPU oracle, single-threaded, on a bounded sample;
@@ -57,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="threshold")
     ap.add_argument("--driver", default="persistent")
+    ap.add_argument("--forbidden", default="auto", choices=["auto", "rescan", "push"],
+                    help="how assignment steps find forbidden colours (default: the library's)")
     ap.add_argument("--batch-graphs", type=int, default=4096,
                     help="graphs of the batched workload (0 = skip the batched leg)")
     ap.add_argument("--batch-steps", type=int, default=3)
@@ -712,7 +715,9 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     if ctx.validate(drp, dcl, stream=stream) != ipgc.IPGC_OK:
         raise SystemExit("input graph failed validation")
-    opts = ipgc.ColorOptions(mode=args.mode, driver=args.driver, validate=False)
+    opts = ipgc.ColorOptions(mode=args.mode, driver=args.driver, validate=False,
+                             forbidden=args.forbidden)
+    pushing = args.driver == "persistent" and args.forbidden in ("auto", "push")
 
     # one traced run (untimed): per-round modes and finalisation rounds for the byte count
     trace = ipgc.trace_buffer(n + 2, local)
@@ -728,7 +733,7 @@ def main():
     t_round_end = tr["t_detect"].astype(np.int64)
     split = r0 - 1 if r0 > 0 else rounds
     per_kernel = [{
-        "kernel": "persistent_kernel<256>",
+        "kernel": "persistent_push_kernel<256>" if pushing else "persistent_kernel<256>",
         "rounds": [1, split],
         "algorithmic_bytes": int(sum(rb[:split])),
         "device_ms": float(t_round_end[split - 1] - tr["t_begin"][0]) / 1e6,
@@ -744,6 +749,8 @@ def main():
         k["algorithmic_gbs"] = k["algorithmic_bytes"] / max(k["device_ms"], 1e-9) / 1e6
     if args.driver == "hostloop":  # round 1, two per later round, the finishing kernel
         launches_per_step = 2 + 2 * (rounds - 1)
+    elif pushing:  # the pushing kernel, then the rescanning one (returns at once)
+        launches_per_step = 2
     else:  # the persistent kernel, then the filtering kernel (returns at once without a hand-over)
         launches_per_step = 2 if opts.filter_degree >= 0 else 1
     del trace, fin
@@ -832,8 +839,11 @@ def main():
             "rounds_topo": int(st.rounds_topo),
             "rounds_data": int(st.rounds_data),
             "schedule": f"{args.mode} (H = 0.6 n), driver {args.driver}",
-            "neighbour_filtering": {"filter_degree": "default (1024)", "start": "default (|WL| <= n/32)",
-                                    "filter_round": int(r0)},
+            "forbidden_colours": ("bitmaps filled by pushes, lower-neighbour lists for conflicts"
+                                  if pushing else "rows rescanned every round"),
+            "neighbour_filtering": ({"filter_degree": "default (1024)",
+                                     "start": "default (|WL| <= n/32)", "filter_round": int(r0)}
+                                    if not pushing else "off (pushing)"),
             "l2": "inputs larger than L2 (col 513 MB vs 129 MB L2); no flush",
             "parallelism": "replicas" if world > 1 else "single GPU",
         },
@@ -851,7 +861,7 @@ def main():
             "launches_per_step": launches_per_step,
             "per_kernel": per_kernel,
             "traffic_source": "profiles/rmat_s22_dram_traffic.md (ncu dram__bytes_read.sum + "
-                              "dram__bytes_write.sum, both kernels, one colouring)"
+                              "dram__bytes_write.sum, both launches, one colouring)"
                               if traffic is not None else "no ncu summary for these kernel sources",
         },
         "e2e": {
