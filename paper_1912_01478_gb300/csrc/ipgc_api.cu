@@ -13,7 +13,8 @@ using ipgc::Params;
 struct ipgc_ctx {
   int device = 0;
   int num_sms = 0;
-  int occ256 = 0, occ512 = 0;  // resident CTAs per SM of the persistent kernel
+  int occ256 = 0, occ512 = 0;  // resident CTAs per SM of the rescanning persistent kernels
+  int pocc256 = 0, pocc512 = 0;  // ... of the pushing kernel
   // workspace for one colouring: tent, worklists, static lists
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -419,12 +420,16 @@ int ipgc_ctx_create(ipgc_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
   if (e == cudaSuccess) e = ipgc::occupancy_persistent(256, &ctx->occ256);
   if (e == cudaSuccess) e = ipgc::occupancy_persistent(512, &ctx->occ512);
+  if (e == cudaSuccess) e = ipgc::occupancy_push(256, &ctx->pocc256);
+  if (e == cudaSuccess) e = ipgc::occupancy_push(512, &ctx->pocc512);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_err, sizeof(int));
   if (e != cudaSuccess) rc = cuda_fail(ctx, e);
-  if (rc == IPGC_OK && (!coop || ctx->occ256 < 1 || ctx->occ512 < 1)) rc = IPGC_ERR_UNSUPPORTED;
+  if (rc == IPGC_OK && (!coop || ctx->occ256 < 1 || ctx->occ512 < 1 || ctx->pocc256 < 1 ||
+                        ctx->pocc512 < 1))
+    rc = IPGC_ERR_UNSUPPORTED;
   if (rc != IPGC_OK) {
     ipgc_ctx_destroy(ctx);
     return rc;
@@ -519,10 +524,12 @@ int ipgc_color_ex(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int3
   IPGC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctrl, 0, sizeof(Ctrl), s));
   const int bs = o.block_size ? o.block_size : ipgc::kBlock;
   int bps = bs == 256 ? ctx->occ256 : ctx->occ512;
+  int pbps = bs == 256 ? ctx->pocc256 : ctx->pocc512;
   if (o.blocks_per_sm > 0 && o.blocks_per_sm < bps) bps = o.blocks_per_sm;
+  if (o.blocks_per_sm > 0 && o.blocks_per_sm < pbps) pbps = o.blocks_per_sm;
   const int blocks = bps * ctx->num_sms;
   if (o.driver == IPGC_DRIVER_PERSISTENT) {
-    IPGC_CUDA(ctx, ipgc::launch_persistent(p, bs, blocks, s));
+    IPGC_CUDA(ctx, ipgc::launch_persistent(p, bs, blocks, pbps * ctx->num_sms, s));
   } else {
     rc = run_hostloop(ctx, p, bs, blocks, s);
     if (rc != IPGC_OK) return rc;

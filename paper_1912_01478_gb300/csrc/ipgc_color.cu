@@ -47,9 +47,13 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(const __
 
 // The whole colouring with forbidden-colour bitmaps (Params::pbits): a
 // separate instantiation, so the kernels that rescan rows keep their
-// register budget.
+// register budget. 2 CTAs of 256 (or 1 of 512) per SM: its round loop needs
+// about 128 registers, and at 80 (3 CTAs) the spills cost more than the
+// extra warps hide (RMAT scale 22: 27.3 ms against 30.7 ms, same GPU).
+constexpr int push_min_blocks(int bs) { return bs >= 512 ? 1 : 2; }
+
 template <int BS>
-__global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_push_kernel(const __grid_constant__ Params p) {
+__global__ void __launch_bounds__(BS, push_min_blocks(BS)) persistent_push_kernel(const __grid_constant__ Params p) {
   __shared__ Smem<BS> sm;
   smem_clear<BS>(sm);
   color_graph<BS, true>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
@@ -179,31 +183,36 @@ cudaError_t with_block_filt(int bs, bool filt, F f) {
 }
 
 cudaError_t occupancy_persistent(int bs, int* blocks_per_sm) {
-  // the smallest of the kernels' occupancies
-  int a = 0, b = 0, c = 0;
+  // the smaller of the rescanning kernels' occupancies
+  int a = 0, b = 0;
   cudaError_t e = with_block(bs, [&](auto B) {
     cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &a, persistent_kernel<decltype(B)::value>, decltype(B)::value, 0);
     if (r == cudaSuccess)
       r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &b, persistent_filt_kernel<decltype(B)::value>, decltype(B)::value, 0);
-    if (r == cudaSuccess)
-      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &c, persistent_push_kernel<decltype(B)::value>, decltype(B)::value, 0);
     return r;
   });
-  *blocks_per_sm = a < b ? (a < c ? a : c) : (b < c ? b : c);
+  *blocks_per_sm = a < b ? a : b;
   return e;
 }
 
-cudaError_t launch_persistent(const Params& p, int bs, int blocks, cudaStream_t s) {
+cudaError_t occupancy_push(int bs, int* blocks_per_sm) {
+  return with_block(bs, [&](auto B) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        blocks_per_sm, persistent_push_kernel<decltype(B)::value>, decltype(B)::value, 0);
+  });
+}
+
+cudaError_t launch_persistent(const Params& p, int bs, int blocks, int push_blocks,
+                              cudaStream_t s) {
   return with_block(bs, [&](auto B) {
     Params pp = p;
     void* args[] = {&pp};
     cudaError_t e = cudaSuccess;
     if (p.pbits)  // pushing; it leaves graphs without a node of degree > t1 to the next kernel
       e = cudaLaunchCooperativeKernel((const void*)persistent_push_kernel<decltype(B)::value>,
-                                      dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+                                      dim3(push_blocks), dim3(decltype(B)::value), args, 0, s);
     if (e == cudaSuccess)
       e = cudaLaunchCooperativeKernel((const void*)persistent_kernel<decltype(B)::value>,
                                       dim3(blocks), dim3(decltype(B)::value), args, 0, s);

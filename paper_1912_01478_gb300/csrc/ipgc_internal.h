@@ -24,8 +24,12 @@ cudaError_t with_block(int bs, F f) {
 }
 
 // Single-graph colouring (ipgc_color.cu); bs = threads per CTA.
-cudaError_t occupancy_persistent(int bs, int* blocks_per_sm);
-cudaError_t launch_persistent(const Params& p, int bs, int blocks, cudaStream_t s);
+cudaError_t occupancy_persistent(int bs, int* blocks_per_sm);  // the rescanning kernels
+cudaError_t occupancy_push(int bs, int* blocks_per_sm);        // the pushing kernel
+// The pushing kernel (when p.pbits) on push_blocks CTAs, then the rescanning
+// kernels on `blocks` CTAs (they return at once when it coloured the graph).
+cudaError_t launch_persistent(const Params& p, int bs, int blocks, int push_blocks,
+                              cudaStream_t s);
 cudaError_t launch_round1(const Params& p, int bs, int blocks, cudaStream_t s);
 cudaError_t launch_assign(const Params& p, int bs, int blocks, int round, int mode, cudaStream_t s);
 cudaError_t launch_detect(const Params& p, int bs, int blocks, int round, int mode, cudaStream_t s);

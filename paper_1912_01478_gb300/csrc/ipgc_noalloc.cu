@@ -145,7 +145,7 @@ extern "C" IPGC_API int ipgc_color_noalloc(const int32_t* rowptr, const int32_t*
   p.max_rounds = n + 1;
   p.timeout_ns = 10000000000ull;
   p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
-  if (launch_persistent(p, 256, ds.occ * ds.sms, s) != cudaSuccess) return IPGC_ERR_CUDA;
+  if (launch_persistent(p, 256, ds.occ * ds.sms, 0, s) != cudaSuccess) return IPGC_ERR_CUDA;
   if (!stats_out) return IPGC_OK;
 
   Ctrl h;

@@ -1713,11 +1713,33 @@ __device__ __forceinline__ int auto_t1(const Params& p, int maxdeg) {
 template <int BS>
 __device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm, bool zero) {
   int m = 0;
-  for (int64_t v = (int64_t)tm.cta * BS + threadIdx.x; v < p.n; v += (int64_t)tm.ncta * BS) {
-    const int s = ld_ro(p.rowptr + v), d = ld_ro(p.rowptr + v + 1) - s;
-    m = max(m, d);
-    if (zero && d > p.t1)
-      for (int i = 0, nw = push_words(d); i < nw; ++i) p.pbits[s + i] = 0u;
+  // four nodes per thread and step: one int4 of row offsets (16-byte aligned
+  // rowptr) and the next offset, so a pass over a large graph keeps many
+  // loads in flight
+  const bool vec = ((uintptr_t)p.rowptr & 15u) == 0;
+  const int64_t n = p.n;
+  for (int64_t v0 = ((int64_t)tm.cta * BS + threadIdx.x) * 4; v0 < n;
+       v0 += (int64_t)tm.ncta * BS * 4) {
+    int r[5];
+    if (vec && v0 + 4 <= n) {
+      const int4 x = __ldg(reinterpret_cast<const int4*>(p.rowptr + v0));
+      r[0] = x.x;
+      r[1] = x.y;
+      r[2] = x.z;
+      r[3] = x.w;
+      r[4] = ld_ro(p.rowptr + v0 + 4);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) r[j] = v0 + j <= n ? ld_ro(p.rowptr + v0 + j) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (v0 + j >= n) break;
+      const int s = r[j], d = r[j + 1] - s;
+      m = max(m, d);
+      if (zero && d > p.t1)
+        for (int i = 0, nw = push_words(d); i < nw; ++i) p.pbits[s + i] = 0u;
+    }
   }
   m = block_max<BS>(sm, m);
   if (threadIdx.x == 0 && m > 0) atomicMax(&p.ctrl->maxdeg, m);
@@ -1809,8 +1831,10 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   if (lead && c->t_start == 0) c->t_start = t0;  // (a pushing kernel before this one may have set it)
   int t1 = p.t1;
   bool pushing = false;
+  // a pushing kernel that left the colouring to this one found the largest degree already
+  const bool known = !PUSH && p.pbits != nullptr && read_shared_word<BS>(&c->push_off, sm) != 0;
   if (p.t1_auto || PUSH) {  // one pass over the row offsets: the largest degree decides t1
-    if (!team_max_degree<BS>(p, sm, tm, PUSH && p.pbits != nullptr)) {
+    if (!known && !team_max_degree<BS>(p, sm, tm, PUSH && p.pbits != nullptr)) {
       if (lead) c->t_end = gtime();
       return;
     }
