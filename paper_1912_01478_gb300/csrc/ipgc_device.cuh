@@ -128,8 +128,8 @@ struct Params {
   // its colour into the bitmaps of its neighbours when it is committed, so
   // the assignment step of v reads the bitmap instead of the row. The
   // conflict step lists its winners (pw: nodes of degree <= t1; pq: the
-  // kPushChunk-entry chunks {v, chunk, gslot, #chunks} of the rows of the
-  // others), and a push phase of the whole team follows it. A node with
+  // kPushChunk-entry chunks {row start, degree, colour, chunk} of the rows of
+  // the others), and a push phase of the whole team follows it. A node with
   // several items also keeps the list of its lower-ID neighbours that are
   // still active (alist/flen/fst/fdead as for neighbour filtering, lower
   // part only; built in round 2, rewritten without finalised entries by the

@@ -171,7 +171,21 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, in
     if (PUSH && pushing) {  // winners: colour 1 into their neighbours' bitmaps
       const bool win = valid && !lose;
       small_push(p, s, win && !big ? d : 0, 1, t1, false);
-      items_push_direct(v, win && big ? num_chunks(d, kPushChunk) : 0, gslot, p.pq, &c->pqcnt);
+      // the others' rows: queued for the push phase after round 1, one lane at a time
+      const int nq = win && big ? num_chunks(d, kPushChunk) : 0;
+      int incl = nq;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int tot = __shfl_sync(FULL, incl, 31);
+      if (tot) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&c->pqcnt, tot);
+        base = __shfl_sync(FULL, base, 0) + incl - nq;
+        for (int j = 0; j < nq; ++j) p.pq[base + j] = make_int4(s, d, 1, j);
+      }
     }
   }
   stage_flush(ss, p.wl[0], &c->cnt[0][B_SMALL]);
@@ -601,6 +615,21 @@ __device__ __forceinline__ void item_assign_push(const Params& p, int v, int s, 
   if (lane_id() == 0) p.tent[v] = t;
 }
 
+// The row of a node of degree d (entries from s) committed with colour t,
+// queued for the push phase in kPushChunk-entry items {s, d, t, chunk}, and
+// asked into L2 meanwhile. One warp, warp-uniform arguments.
+__device__ __forceinline__ void push_queue(const Params& p, int s, int d, int t) {
+  const int lane = lane_id();
+  const int n = num_chunks(d, kPushChunk);
+  int base = 0;
+  if (lane == 0) {
+    base = atomicAdd(&p.ctrl->pqcnt, n);
+    prefetch_l2(p, s, (int64_t)s + d);
+  }
+  base = __shfl_sync(FULL, base, 0);
+  for (int j = lane; j < n; j += 32) p.pq[base + j] = make_int4(s, d, t, j);
+}
+
 // Conflict step for work item (v, c); the warp that finishes v's last item
 // commits v or pushes its items to the next worklist.
 __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, int v, int s, int d,
@@ -670,9 +699,8 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
       if (p.fin) p.fin[v] = round;
     }
   }
-  if (wst)  // pushing: the push phase after this step ORs t into the neighbours' bitmaps
-    items_push_direct(v, finisher && !lose && lane == 0 ? num_chunks(d, kPushChunk) : 0, gslot,
-                      p.pq, &p.ctrl->pqcnt);
+  if (wst && finisher && !lose)  // pushing: the push phase after this step ORs t into the
+    push_queue(p, s, d, t);        // neighbours' bitmaps
 }
 
 // ------------------------------------- lower-neighbour lists (with pushing) --
@@ -809,17 +837,25 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
   seen = __reduce_add_sync(FULL, seen);
   int finisher = 0, lose = 0;
   if (lane == 0) {
-    if (hit) atomicOr(&p.flag[gslot], 1);
-    if (dead) atomicAdd(p.fdead + gslot, dead);
-    if (seen) atomicAdd(p.done_a + gslot, seen);
-    __threadfence();
-    finisher = atomicAdd(&p.done_d[gslot], 1) == nch - 1;
-    if (finisher) {
+    int D = dead, S = seen;
+    if (nch == 1) {  // the only item: nothing to merge
+      finisher = 1;
+      lose = hit;
+    } else {
+      if (hit) atomicOr(&p.flag[gslot], 1);
+      if (dead) atomicAdd(p.fdead + gslot, dead);
+      if (seen) atomicAdd(p.done_a + gslot, seen);
       __threadfence();
-      lose = atomicExch(&p.flag[gslot], 0) != 0;
-      p.done_d[gslot] = 0;
-      const int D = atomicExch(p.fdead + gslot, 0);
-      const int S = atomicExch(p.done_a + gslot, 0);
+      finisher = atomicAdd(&p.done_d[gslot], 1) == nch - 1;
+      if (finisher) {
+        __threadfence();
+        lose = atomicExch(&p.flag[gslot], 0) != 0;
+        p.done_d[gslot] = 0;
+        D = atomicExch(p.fdead + gslot, 0);
+        S = atomicExch(p.done_a + gslot, 0);
+      }
+    }
+    if (finisher) {
       const bool rw = D > 0 && 4 * (int64_t)D >= (int64_t)S;
       if ((st & 6) == 6) p.flen[cur][gslot] = make_int2(0, 0);  // rewritten: the old buffer is free
       p.fst[gslot] = nb | 4 | (rw ? 2 : 0);
@@ -830,8 +866,7 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
   const int nxt_items = lists_next ? max(1, num_chunks(L, p.chunk)) : num_chunks(d, p.chunk);
   items_push(stage, v, (push && finisher && lose && lane == 0) ? nxt_items : 0, gslot,
              p.items[nxt], &p.ctrl->icnt[nxt]);
-  items_push_direct(v, (finisher && !lose && lane == 0) ? num_chunks(d, kPushChunk) : 0, gslot,
-                    p.pq, &p.ctrl->pqcnt);
+  if (finisher && !lose) push_queue(p, s, d, t);
   if (finisher && lane == 0) {
     if (lose) {
       acc.nbig += 1;
@@ -1612,13 +1647,10 @@ __device__ __noinline__ void push_phase(const Params& p, int nq, int nw, int t1,
   const int units = nq + (nw + 31) / 32;
   for (int k = gwarp; k < units; k += nwarps) {
     if (k < nq) {
-      const int4 it = ld_cg4(p.pq + k);
-      const int v = it.x;
-      const int s = ld_ro(p.rowptr + v), e = ld_ro(p.rowptr + v + 1);
-      const int t = ld_cg(p.color + v);
-      const int64_t lo = (int64_t)s + (int64_t)it.y * kPushChunk;
-      const int64_t hi = min((int64_t)e, lo + kPushChunk);
-      push_range(p, lo, hi, t, t1);
+      const int4 it = ld_cg4(p.pq + k);  // {row start, degree, colour, chunk}
+      const int64_t lo = (int64_t)it.x + (int64_t)it.w * kPushChunk;
+      const int64_t hi = min((int64_t)it.x + it.y, lo + kPushChunk);
+      push_range(p, lo, hi, it.z, t1);
     } else {
       const int i = (k - nq) * 32 + lane;
       int s = 0, d = 0, t = 1;
