@@ -47,10 +47,8 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(const __
 
 // The whole colouring with forbidden-colour bitmaps (Params::pbits): a
 // separate instantiation, so the kernels that rescan rows keep their
-// register budget. 2 CTAs of 256 (or 1 of 512) per SM: its round loop needs
-// about 128 registers, and at 80 (3 CTAs) the spills cost more than the
-// extra warps hide (RMAT scale 22: 27.3 ms against 30.7 ms, same GPU).
-constexpr int push_min_blocks(int bs) { return bs >= 512 ? 1 : 2; }
+// register budget (the occupancy of each kernel sets its own grid size).
+constexpr int push_min_blocks(int bs) { return min_blocks(bs); }
 
 template <int BS>
 __global__ void __launch_bounds__(BS, push_min_blocks(BS)) persistent_push_kernel(const __grid_constant__ Params p) {

@@ -35,7 +35,7 @@ constexpr int kShrinkMinPush = 64;  // ... with pushing
 constexpr int kStageSmall = 128; // per-warp staging of low-degree pushes
 constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
 constexpr int kPushMaxC = 32 * kGWords;  // forbidden-colour bitmaps hold colours 1..2048
-constexpr int kPushChunk = 256;  // row entries per queued push item (one warp window)
+constexpr int kPushChunk = 128;  // row entries per queued push item (one warp window)
 
 // Per-colouring control block in device memory. Zeroed before every launch.
 struct Ctrl {

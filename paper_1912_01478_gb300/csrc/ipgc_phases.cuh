@@ -334,18 +334,23 @@ __device__ __forceinline__ int first_free_64(int nw, Get get) {
   return 0;
 }
 
-constexpr int kGather = 8;             // neighbour entries per lane per window
+// Neighbour entries per lane per window: 4 (one int4). With 8 the loops
+// needed more registers than 3 CTAs of 256 per SM leave (80 per thread) and
+// spilled; 4 with 24 warps per SM beat 8 with 16 (RMAT scale 22: 23.9 ms
+// against 25.6, road 5.3 against 6.3, same GPU).
+constexpr int kGather = 4;
 constexpr int kWindow = 32 * kGather;  // neighbour entries per warp per window
 
 // One window of the neighbour array: the kWindow entries at absolute index
-// a + i (a a multiple of 4), lane l holding entries 4l..4l+3 and
-// 128+4l..128+4l+3, read as int4 where the array is 16-byte aligned and the
-// four entries all lie in [lo, hi); entries outside [lo, hi) read `none`.
+// a + i (a a multiple of 4), lane l holding entries 4l..4l+3 (and
+// 128h+4l..128h+4l+3 for h < kGather / 4), read as int4 where the array is
+// 16-byte aligned and the four entries all lie in [lo, hi); entries outside
+// [lo, hi) read `none`.
 __device__ __forceinline__ void load_window(const Params& p, int64_t a, int64_t lo, int64_t hi,
                                             int none, int (&u)[kGather]) {
   const int lane = lane_id();
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < kGather / 4; ++h) {
     const int64_t q = a + 128 * h + 4 * lane;
     if (p.col_vec && q >= lo && q + 3 < hi) {
       const int4 x = __ldg(reinterpret_cast<const int4*>(p.col + q));
@@ -367,7 +372,7 @@ __device__ __forceinline__ void load_window_rw(const int32_t* arr, int64_t a, in
                                                int none, int (&u)[kGather]) {
   const int lane = lane_id();
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < kGather / 4; ++h) {
     const int64_t q = a + 128 * h + 4 * lane;
     if (q >= lo && q + 3 < hi) {
       const int4 x = ld_cg4(reinterpret_cast<const int4*>(arr + q));
