@@ -47,8 +47,10 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(const __
 
 // The whole colouring with forbidden-colour bitmaps (Params::pbits): a
 // separate instantiation, so the kernels that rescan rows keep their
-// register budget (the occupancy of each kernel sets its own grid size).
-constexpr int push_min_blocks(int bs) { return min_blocks(bs); }
+// register budget (the occupancy of each kernel sets its own grid size):
+// 3 CTAs of 256 per SM (80 registers), where 4 (64 registers) spilled and
+// lost 4 % on RMAT scale 22.
+constexpr int push_min_blocks(int bs) { return bs >= 512 ? 2 : 3; }
 
 template <int BS>
 __global__ void __launch_bounds__(BS, push_min_blocks(BS)) persistent_push_kernel(const __grid_constant__ Params p) {

@@ -12,9 +12,12 @@ namespace ipgc {
 
 enum { MODE_TOPO = IPGC_MODE_TOPO, MODE_DATA = IPGC_MODE_DATA };
 
-// Resident CTAs per SM each block size is compiled for: 512 threads x 2 caps
-// a thread at 64 registers, 256 x 3 at 85.
-constexpr int min_blocks(int bs) { return bs >= 512 ? 2 : 3; }
+// Resident CTAs per SM each block size is compiled for: 512 threads x 2 or
+// 256 x 4 cap a thread at 64 registers. The rescanning kernels are mostly
+// the packed low-degree loop, which wants warps (road 5.3 -> 3.6 ms going
+// from 3 CTAs of 256 to 4, same GPU); the pushing kernel keeps 3 (its own
+// bound, in ipgc_color.cu).
+constexpr int min_blocks(int bs) { return bs >= 512 ? 2 : 4; }
 
 template <int BS>
 struct Smem {
@@ -231,7 +234,7 @@ __device__ __forceinline__ int small_owner(int off, int e) {
   return j;
 }
 
-constexpr int kSmallUnroll = 8;
+constexpr int kSmallUnroll = 4;
 
 // First-fit colour of each lane's node into tent[v]. wm: this warp's 32 * kSmallWords words.
 __device__ __forceinline__ void small_assign(const Params& p, int v, int s, int d, unsigned* wm) {
