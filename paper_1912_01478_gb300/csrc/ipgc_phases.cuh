@@ -774,6 +774,7 @@ __device__ __forceinline__ void item_assign_plist(const Params& p, int v, int s,
                                                   int nch, int gslot) {
   if (c == 0) item_assign_push(p, v, s, d);
   const int st = ld_cg(p.fst + gslot);
+  const int L0 = ld_cg(&p.flen[0][gslot].x), L1 = ld_cg(&p.flen[1][gslot].x);
   if (!(st & 4)) {  // built from row chunk c (the items of a node without a list are its row's)
     const int64_t lo = (int64_t)s + (int64_t)c * p.chunk;
     const int64_t hi = min((int64_t)s + d, lo + p.chunk);
@@ -781,7 +782,7 @@ __device__ __forceinline__ void item_assign_plist(const Params& p, int v, int s,
       plist_append(p, p.col, true, lo, hi, v, s, p.alist[0], &p.flen[0][gslot].x);
   } else if (st & 2) {
     const int cur = st & 1;
-    const int L = ld_cg(&p.flen[cur][gslot].x);
+    const int L = cur ? L1 : L0;
     const int64_t lo = s + (int64_t)L * c / nch, hi = s + (int64_t)L * (c + 1) / nch;
     plist_append(p, p.alist[cur], false, lo, hi, v, s, p.alist[cur ^ 1],
                  &p.flen[cur ^ 1][gslot].x);
@@ -803,9 +804,11 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
   const uint64_t pol = l2_keep_policy();
   const int t = ld_cg(p.tent + v);
   const int st = ld_cg(p.fst + gslot);
+  // both buffers' lengths together with the state: one round trip, not two
+  const int L0 = ld_cg(&p.flen[0][gslot].x), L1 = ld_cg(&p.flen[1][gslot].x);
   const int cur = st & 1;
   const int nb = !(st & 4) ? 0 : ((st & 2) ? cur ^ 1 : cur);
-  const int L = ld_cg(&p.flen[nb][gslot].x);
+  const int L = nb ? L1 : L0;
   const int32_t* lst = p.alist[nb];
   const int64_t lo = s + (int64_t)L * c / nch, hi = s + (int64_t)L * (c + 1) / nch;
   bool hit = false;
