@@ -64,6 +64,9 @@ struct Ctrl {
   int32_t pwcnt;                   // winners of the current conflict step still to push
   int32_t push_off;                // the pushing kernel found no node of degree > t1 and left
                                    // the colouring to the rescanning kernel launched after it
+  int32_t late_at[2];              // pushing: the latest round of each parity ran late (no push
+                                   // phase); parity slots, like maxc_start: CTA 0 writes round
+                                   // r's while slower CTAs may still read round r - 1's
   int32_t push_on;                 // forbidden-colour bitmaps in use (some degree > t1)
   // arrival counters of the grid barrier's groups, one 32-byte sector each
   uint32_t bar_grp[kBarGroups][8];

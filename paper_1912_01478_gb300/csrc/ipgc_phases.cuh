@@ -33,7 +33,8 @@ struct Smem {
   int mode_b;  // broadcast of the round's mode (learned policy)
   unsigned red2[W];
   unsigned red3[W];
-  int rvb[16];  // round state read from the control block once per CTA
+  unsigned red4[W];
+  int rvb[24];  // round state read from the control block once per CTA
 };
 
 template <int BS>
@@ -73,6 +74,7 @@ struct PhaseAcc {
   unsigned long long dsum = 0;  // degrees of the nodes this thread pushed
   unsigned long long nbig = 0;  // high-degree nodes this thread pushed
   unsigned long long nsm = 0;   // low-degree losers counted, not pushed (worklist rebuild)
+  unsigned nodd = 0;            // pushing: losers that keep the next round from running late
 };
 
 // One CTA-wide reduction of the accumulators, then one atomic each.
@@ -84,12 +86,14 @@ __device__ __forceinline__ void phase_commit(const Params& p, Smem<BS>& sm, cons
   const unsigned long long ds = warp_sum_u64(a.dsum);
   const unsigned nb = __reduce_add_sync(FULL, (unsigned)a.nbig);
   const unsigned ns = __reduce_add_sync(FULL, (unsigned)a.nsm);
+  const unsigned no = __reduce_add_sync(FULL, a.nodd);
   __syncthreads();  // previous users of the scratch slots are done
   if (lane == 0) {
     sm.red[warp] = m;
     sm.red64[warp] = ds;
     sm.red2[warp] = nb;
     sm.red3[warp] = ns;
+    sm.red4[warp] = no;
   }
   __syncthreads();
   if (warp == 0) {
@@ -98,11 +102,13 @@ __device__ __forceinline__ void phase_commit(const Params& p, Smem<BS>& sm, cons
     const unsigned long long dd = warp_sum_u64(in ? sm.red64[lane] : 0ull);
     const unsigned bb = __reduce_add_sync(FULL, in ? sm.red2[lane] : 0u);
     const unsigned ss = __reduce_add_sync(FULL, in ? sm.red3[lane] : 0u);
+    const unsigned oo = __reduce_add_sync(FULL, in ? sm.red4[lane] : 0u);
     if (lane == 0) {
       if (mm > 0) atomicMax(&p.ctrl->maxc, mm);
       if (dd) atomicAdd(&p.ctrl->dsum[nxt], dd);
       if (bb) atomicAdd(&p.ctrl->cnt[nxt][B_BIG], (int)bb);
       if (ss) atomicAdd(&p.ctrl->cnt[nxt][B_SMALL], (int)ss);
+      if (oo) atomicAdd(&p.ctrl->cnt[nxt][2], (int)oo);
     }
   }
 }
@@ -638,6 +644,33 @@ __device__ __forceinline__ void push_queue(const Params& p, int s, int d, int t)
   for (int j = lane; j < n; j += 32) p.pq[base + j] = make_int4(s, d, t, j);
 }
 
+// Colour t into the bitmaps of the still-active, bitmap-keeping entries of
+// list range [lo, hi) of lst (a late round's winner pushing along its list
+// of active lower-ID neighbours). One warp.
+inline __device__ __noinline__ void push_list(const Params& p, const int32_t* lst, int64_t lo,
+                                              int64_t hi, int t, int t1) {
+  const uint64_t pol = l2_keep_policy();
+  for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
+    int u[kGather];
+    load_window_rw(lst, a, lo, hi, -1, u);
+    int sw[kGather], ew[kGather], cw[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      sw[q] = 0;
+      ew[q] = 0;
+      cw[q] = 1;
+      if (u[q] >= 0) {
+        sw[q] = ld_ro(p.rowptr + u[q]);
+        ew[q] = ld_ro(p.rowptr + u[q] + 1);
+        cw[q] = ld_keep(p.color + u[q], pol);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGather; ++q)
+      if (cw[q] == 0 && ew[q] - sw[q] > t1) push_to(p, sw[q], ew[q] - sw[q], t);
+  }
+}
+
 // Conflict step for work item (v, c); the warp that finishes v's last item
 // commits v or pushes its items to the next worklist.
 __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, int v, int s, int d,
@@ -709,6 +742,7 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
   }
   if (wst && finisher && !lose)  // pushing: the push phase after this step ORs t into the
     push_queue(p, s, d, t);        // neighbours' bitmaps
+  if (wst && finisher && lose && lane == 0) acc.nodd += 1;  // not a list node
 }
 
 // ------------------------------------- lower-neighbour lists (with pushing) --
@@ -767,14 +801,77 @@ __device__ __forceinline__ void plist_append(const Params& p, const int32_t* src
   }
 }
 
+// Entries [lo, hi) of v's list src after a late round: the colours of the
+// finalised ones into v's bitmap (those <= min(d, kPushMaxC)); with dst, the
+// active ones appended to the list there (the rewrite). One warp.
+__device__ __forceinline__ void plist_pull(const Params& p, const int32_t* src, int64_t lo,
+                                           int64_t hi, int64_t s, int d, int32_t* dst, int* len) {
+  const int lane = lane_id();
+  const uint64_t pol = l2_keep_policy();
+  const int lim = min(d, kPushMaxC);
+  for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
+    int u[kGather];
+    load_window_rw(src, a, lo, hi, -1, u);
+    int cc[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) cc[q] = u[q] >= 0 ? ld_keep(p.color + u[q], pol) : -1;
+    int k = 0;
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) {
+      if (cc[q] > 0 && cc[q] <= lim)
+        atomicOr(p.pbits + s + ((cc[q] - 1) >> 5), 1u << ((cc[q] - 1) & 31));
+      k += cc[q] == 0;
+    }
+    if (!dst) continue;
+    int x = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    const int tot = __shfl_sync(FULL, x, 31);
+    if (tot) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(len, tot);
+      int o = __shfl_sync(FULL, base, 0) + x - k;
+#pragma unroll
+      for (int q = 0; q < kGather; ++q)
+        if (cc[q] == 0) dst[s + o++] = u[q];
+    }
+  }
+}
+
 // Assignment step for work item c of nch of node v with a merge-state slot:
 // item 0 takes tent[v] from the bitmap; every item builds or rewrites its
 // share of the list.
 __device__ __forceinline__ void item_assign_plist(const Params& p, int v, int s, int d, int c,
-                                                  int nch, int gslot) {
-  if (c == 0) item_assign_push(p, v, s, d);
+                                                  int nch, int gslot, bool pull) {
   const int st = ld_cg(p.fst + gslot);
   const int L0 = ld_cg(&p.flen[0][gslot].x), L1 = ld_cg(&p.flen[1][gslot].x);
+  if (pull && (st & 4)) {  // after a late round: collect its lower-ID winners from the list
+    const int cur = st & 1;
+    const int L = cur ? L1 : L0;
+    const int64_t lo = s + (int64_t)L * c / nch, hi = s + (int64_t)L * (c + 1) / nch;
+    plist_pull(p, p.alist[cur], lo, hi, s, d, (st & 2) ? p.alist[cur ^ 1] : nullptr,
+               &p.flen[cur ^ 1][gslot].x);
+    __syncwarp();
+    __threadfence();
+    __syncwarp();
+    if (nch == 1) {
+      item_assign_push(p, v, s, d);
+      return;
+    }
+    int last = 0;  // every item of v has collected its share: the last one takes tent[v]
+    if (lane_id() == 0) last = atomicAdd(&p.done_a[gslot], 1) == nch - 1;
+    last = __shfl_sync(FULL, last, 0);
+    if (last) {
+      __threadfence();
+      item_assign_push(p, v, s, d);
+      if (lane_id() == 0) p.done_a[gslot] = 0;
+    }
+    return;
+  }
+  if (c == 0) item_assign_push(p, v, s, d);
   if (!(st & 4)) {  // built from row chunk c (the items of a node without a list are its row's)
     const int64_t lo = (int64_t)s + (int64_t)c * p.chunk;
     const int64_t hi = min((int64_t)s + d, lo + p.chunk);
@@ -799,7 +896,7 @@ __device__ __forceinline__ void item_assign_plist(const Params& p, int v, int s,
 __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& stage, int v, int s,
                                                   int d, int c, int nch, int gslot, int nxt,
                                                   PhaseAcc& acc, int round, bool push,
-                                                  bool lists_next) {
+                                                  bool lists_next, bool late, int t1) {
   const int lane = lane_id();
   const uint64_t pol = l2_keep_policy();
   const int t = ld_cg(p.tent + v);
@@ -877,7 +974,13 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
   const int nxt_items = lists_next ? max(1, num_chunks(L, p.chunk)) : num_chunks(d, p.chunk);
   items_push(stage, v, (push && finisher && lose && lane == 0) ? nxt_items : 0, gslot,
              p.items[nxt], &p.ctrl->icnt[nxt]);
-  if (finisher && !lose) push_queue(p, s, d, t);
+  if (finisher && !lose) {
+    if (late && nch == 1)  // the list is v's active lower-ID neighbours: push along it
+      push_list(p, lst, lo, hi, t, t1);
+    else
+      push_queue(p, s, d, t);
+  }
+  if (finisher && lose && lane == 0 && nxt_items > 1) acc.nodd += 1;
   if (finisher && lane == 0) {
     if (lose) {
       acc.nbig += 1;
@@ -1242,6 +1345,9 @@ struct RoundView {
   int t1;      // the low-degree bound in use
   int filt;    // nodes of degree > filt_deg read filtered lists this round
   int push;    // nodes of degree > t1 read their forbidden-colour bitmaps this round
+  int odd;     // pushing: worklist nodes that are not list nodes with one work item
+  int late;    // pushing: this round runs late (winners push along their lists, no push phase)
+  int pull;    // pushing: the previous round ran late (list nodes collect lower-ID winners)
   unsigned long long dsum;  // degree sum of the worklist
 };
 
@@ -1255,12 +1361,12 @@ __device__ __forceinline__ RoundView read_round(const Params& p, int r, Smem<BS>
   if (threadIdx.x < 32) {
     const Ctrl* c = p.ctrl;
     const int32_t* dsum = reinterpret_cast<const int32_t*>(&c->dsum[par]);
-    const int32_t* src[12] = {&c->cnt[par][B_SMALL], &c->cnt[par][B_BIG], &c->icnt[par], &c->nistat,
+    const int32_t* src[14] = {&c->cnt[par][B_SMALL], &c->cnt[par][B_BIG], &c->icnt[par], &c->nistat,
                               &c->ficnt[par],        &c->t1,             &c->maxc,       dsum,
                               dsum + 1,              &c->handoff_round,  &c->maxc_start[(r - 1) & 1],
-                              &c->push_on};
+                              &c->push_on,           &c->cnt[par][2],    &c->late_at[(r - 1) & 1]};
     const int lane = lane_id();
-    if (lane < 12) sm.rvb[lane] = ld_cg(src[lane]);
+    if (lane < 14) sm.rvb[lane] = ld_cg(src[lane]);
   }
   __syncthreads();
   RoundView rv;
@@ -1284,6 +1390,9 @@ __device__ __forceinline__ RoundView read_round(const Params& p, int r, Smem<BS>
   // <= kPushMaxC - 2: round r - 1 adds at most 1, so every tentative colour of
   // round r is <= kPushMaxC and the bitmaps hold it
   rv.push = p.pbits != nullptr && sm.rvb[11] != 0 && maxc_prev <= kPushMaxC - 2;
+  rv.odd = sm.rvb[12];
+  rv.late = 0;  // decided with the mode
+  rv.pull = rv.push && r >= 3 && sm.rvb[13] != 0;
   return rv;
 }
 
@@ -1291,9 +1400,9 @@ __device__ __forceinline__ RoundView read_round(const Params& p, int r, Smem<BS>
 template <int BS>
 __device__ __forceinline__ int read_shared_word(const int32_t* w, Smem<BS>& sm) {
   __syncthreads();  // earlier readers of the slot are done
-  if (threadIdx.x == 0) sm.rvb[15] = ld_cg(w);
+  if (threadIdx.x == 0) sm.rvb[23] = ld_cg(w);
   __syncthreads();
-  return sm.rvb[15];
+  return sm.rvb[23];
 }
 
 __device__ __forceinline__ int decide_mode(const Params& p, int64_t total) {
@@ -1339,6 +1448,7 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
   c->dsum[nxt] = 0;
   c->pqcnt = 0;
   c->pwcnt = 0;
+  c->late_at[r & 1] = rv.late ? 1 : 0;
   c->rounds = r;
   c->maxc_start[r & 1] = rv.maxc;
   c->mode_at[r & 1] = rv.mode;
@@ -1379,7 +1489,7 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
 template <int BS>
 __device__ __forceinline__ void assign_items(const Params& p, Smem<BS>& sm, const int4* items,
                                              int count, bool topo, int maxc, bool pushing,
-                                             Team tm) {
+                                             bool pull, Team tm) {
   const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   unsigned* wb = sm.wbits[warp];
@@ -1387,7 +1497,7 @@ __device__ __forceinline__ void assign_items(const Params& p, Smem<BS>& sm, cons
             [&](int v, int c, int gslot, int nch, int s, int d) {
               if (pushing) {
                 if (gslot >= 0)
-                  item_assign_plist(p, v, s, d, c, nch, gslot);
+                  item_assign_plist(p, v, s, d, c, nch, gslot, pull);
                 else if (c == 0)
                   item_assign_push(p, v, s, d);
               } else {
@@ -1453,7 +1563,7 @@ __device__ void assign_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
   if (FILT && rv.filt && (topo || rv.round == rv.r0)) {
     if (gwarp < count) assign_mixed<BS>(p, sm, items, count, rv, tm);
   } else {
-    assign_items<BS>(p, sm, items, count, topo, rv.maxc, PUSH && rv.push, tm);
+    assign_items<BS>(p, sm, items, count, topo, rv.maxc, PUSH && rv.push, PUSH && rv.pull, tm);
     if (FILT && rv.filt && gwarp < rv.ficnt) assign_fitems<BS>(p, sm, rv, tm);
   }
   assign_small_nodes<BS>(p, sm, rv, tm);
@@ -1464,7 +1574,7 @@ template <int BS>
 __device__ __forceinline__ PhaseAcc detect_items(const Params& p, ItemStage& stage,
                                                  const int4* items, int count, bool topo,
                                                  int round, int nxt, WarpStage* wst,
-                                                 bool lists_next, Team tm) {
+                                                 bool lists_next, bool late, int t1, Team tm) {
   const int warp = threadIdx.x >> 5;
   const int gwarp = tm.cta * (BS / 32) + warp, nwarps = tm.ncta * (BS / 32);
   PhaseAcc acc;
@@ -1474,7 +1584,7 @@ __device__ __forceinline__ PhaseAcc detect_items(const Params& p, ItemStage& sta
             [&](int v, int cidx, int gslot, int nch, int s, int d) {
               if (wst && gslot >= 0)
                 item_detect_plist(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round, push,
-                                  lists_next);
+                                  lists_next, late, t1);
               else
                 item_detect(p, stage, v, s, d, cidx, nch, gslot, nxt, acc, round, push, wst);
             });
@@ -1577,6 +1687,7 @@ __device__ __forceinline__ void acc_merge(PhaseAcc& a, const PhaseAcc& b) {
   a.dsum += b.dsum;
   a.nbig += b.nbig;
   a.nsm += b.nsm;
+  a.nodd += b.nodd;
 }
 
 // Worklist rebuild (the discard-and-rebuild hybrid of Nasre et al., which the
@@ -1636,7 +1747,7 @@ __device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
     if (gwarp < count) acc_merge(acc, detect_mixed<BS>(p, sm, stage, items, count, rv, tm));
   } else {
     acc_merge(acc, detect_items<BS>(p, stage, items, count, topo, rv.round, nxt, wst,
-                                    rv.maxc <= kPushMaxC - 2, tm));
+                                    rv.maxc <= kPushMaxC - 2, PUSH && rv.late, rv.t1, tm));
     if (FILT && rv.filt && gwarp < rv.ficnt)
       acc_merge(acc, detect_fitems<BS>(p, sm, stage, rv, tm));
   }
@@ -1810,6 +1921,15 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       break;
     }
     rv.mode = decide_mode_block<BS>(p, rv, total, sm);
+    // pushing runs a round late when every active node keeps a list of one
+    // work item (rounds after 2, data-driven under the threshold or data
+    // rule, which never go back to topology-driven once |WL| is small): the
+    // active edges are then all on the lists, a winner pushes along its own
+    // list (its active lower-ID neighbours) and the next round's list nodes
+    // collect their lower-ID winners from theirs, so no push phase is needed
+    rv.late = PUSH && rv.push && r >= 3 && rv.mode == MODE_DATA && rv.nsmall == 0 &&
+              rv.odd == 0 && (p.policy == IPGC_MODE_THRESHOLD || p.policy == IPGC_MODE_DATA) &&
+              !p.wl_rebuild;
     if (p.wl_rebuild && rv.mode == MODE_DATA &&
         (r == 2 || ld_cg(&c->mode_at[(r - 1) & 1]) == MODE_TOPO)) {
       rebuild_worklists<BS>(p, sm, rv, tm);
@@ -1846,11 +1966,11 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
     if (PUSH && rv.push) {
       __syncthreads();  // the previous readers of the slots are done
       if (threadIdx.x == 0) {
-        sm.rvb[12] = ld_cg(&c->pqcnt);
-        sm.rvb[13] = ld_cg(&c->pwcnt);
+        sm.rvb[20] = ld_cg(&c->pqcnt);
+        sm.rvb[21] = ld_cg(&c->pwcnt);
       }
       __syncthreads();
-      const int q = sm.rvb[12], w = sm.rvb[13];
+      const int q = sm.rvb[20], w = sm.rvb[21];
       if (q > 0 || w > 0) {
         const uint64_t tp = lead && p.trace && r <= p.trace_cap ? gtime() : 0;
         push_phase<BS>(p, q, w, rv.t1, tm);
