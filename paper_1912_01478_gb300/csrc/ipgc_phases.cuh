@@ -1945,8 +1945,9 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       const int64_t units = (int64_t)rv.icnt + (FILT ? rv.ficnt : 0) + ((int64_t)rv.nsmall + 31) / 32;
       const int64_t want = (units + (BS / 32) - 1) / (BS / 32);
       // (with pushing a high-degree winner's whole row is pushed after the
-      // conflict step, one warp per kPushChunk entries: keep more CTAs)
-      const int kmin = PUSH && rv.push ? kShrinkMinPush : kShrinkMin;
+      // conflict step, one warp per kPushChunk entries: keep more CTAs, except
+      // in late rounds, whose winners push along their short lists)
+      const int kmin = PUSH && rv.push && !rv.late ? kShrinkMinPush : kShrinkMin;
       const int k = (int)(want > kmin ? want : kmin);
       if (4 * k <= tm.ncta) {
         if (tm.cta >= k) break;
