@@ -115,6 +115,26 @@ def test_workspace_size(lib):
     assert lib.ipgc_workspace_size(1000, 8000, ctypes.byref(o)) > lib.ipgc_workspace_size(1000, 8000, None)
 
 
+def test_workspace_size_by_forbidden_colour_source(lib):
+    # the default (persistent driver) pushes: rescanning's arrays plus the
+    # bitmaps (4 bytes per entry), the winners list (4 per node) and the
+    # push queue; rescanning with filtering holds the two list buffers (8
+    # bytes per entry), without filtering neither; the host-loop driver
+    # rescans whatever `forbidden` says by default
+    n, nnz = 4_194_304, 128_304_280
+
+    def size(**kw):
+        return lib.ipgc_workspace_size(n, nnz, ctypes.byref(ipgc.ColorOptions(**kw).to_c()))
+
+    auto, push = size(), size(forbidden="push")
+    rescan, plain = size(forbidden="rescan"), size(forbidden="rescan", filter_degree=-1)
+    assert auto == push
+    assert size(driver="hostloop") == rescan
+    assert rescan - plain >= 8 * nnz
+    # + bitmaps (4 nnz) + winners (4 n) + queue, - the filtered items (2 x 16 B per item)
+    assert 3.5 * nnz < push - rescan < 4 * nnz + 4 * n + 16 * (nnz // 128 + n + 1)
+
+
 def test_host_validation(lib):
     rp, cl = graphgen.er(200, 600, seed=5)
     assert ipgc.validate_host(rp, cl) == ipgc.IPGC_OK
