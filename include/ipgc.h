@@ -253,7 +253,10 @@ IPGC_API int ipgc_validate_csr(ipgc_ctx* ctx, const int32_t* rowptr, const int32
  * smaller; teams are gang-scheduled on aligned blocks of CTAs, largest
  * first, and graphs with k = 1 are taken one CTA each from a shared queue. Options in `base` apply
  * to every graph (trace, fin_round, driver, blocks_per_sm and fault_inject
- * are ignored).
+ * are ignored). Unless base.forbidden is IPGC_FORBIDDEN_RESCAN, graphs with a
+ * node of degree > t1 are coloured with forbidden-colour bitmaps (a first
+ * launch; see ipgc_options.forbidden) and the others by rescanning rows (a
+ * second launch, with a schedule of its own).
  */
 typedef struct ipgc_batch_options {
   ipgc_options base;     /* defaults as ipgc_options_default, but validate = 0 */
@@ -277,7 +280,8 @@ IPGC_API void ipgc_batch_options_default(ipgc_batch_options* opt);
  *   per_graph_stats  host pointer to G records, or NULL (then the call only
  *                enqueues work on `stream`)
  * The context keeps a batched workspace (about 12 bytes per node, 16 bytes
- * per work item and 256 bytes per large node), grown on demand.
+ * per work item and 256 bytes per large node; with bitmaps also 12 bytes per
+ * entry and 4 per node), grown on demand.
  * Returns IPGC_OK or the first per-graph error (IPGC_ERR_INVALID for a bad
  * graph when base.validate is set, IPGC_ERR_TIMEOUT, IPGC_ERR_NO_CONVERGE),
  * IPGC_ERR_OOM, IPGC_ERR_CUDA.

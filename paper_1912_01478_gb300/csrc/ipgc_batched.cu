@@ -36,43 +36,81 @@ struct BatchParams {
 // global job order, so the team of the earliest unfinished job can always
 // meet at its barriers and no two teams wait on each other in a cycle. Then
 // every CTA takes single-CTA graphs from the shared counter.
+// The jobs of one CTA, then single-CTA graphs from the shared counter. With
+// PUSH every graph is coloured with forbidden-colour bitmaps (Params::pbits),
+// except those without a node above t1, which it leaves to the rescanning
+// kernel launched after it (ctrl->push_off); without PUSH a graph given
+// bitmaps is skipped unless the pushing kernel left it.
+template <int BS, bool PUSH>
+__device__ __forceinline__ void batched_jobs(const BatchParams& bp, Smem<BS>& sm, int* s_k) {
+  // one call site of the round loop (two inlined copies cost registers)
+  int j = bp.cta_off[blockIdx.x];
+  const int jend = bp.cta_off[blockIdx.x + 1];
+  for (;;) {
+    int g;
+    Team tm{0, 1};
+    if (j < jend) {
+      const int4 jb = bp.jobs[j++];
+      g = jb.x;
+      tm = Team{jb.y, jb.z};
+    } else {
+      __syncthreads();
+      if (threadIdx.x == 0) *s_k = atomicAdd(bp.solo_next, 1);
+      __syncthreads();
+      const int k = *s_k;
+      if (k >= bp.nsolo) break;
+      g = bp.solo_list[k];
+    }
+    const Params& gp = bp.params[g];
+    if (!PUSH && gp.pbits && ld_cg(&gp.ctrl->push_off) == 0) continue;  // coloured by pushing
+    color_graph<BS, PUSH>(gp, sm, tm);
+  }
+}
+
 template <int BS>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) batched_kernel(BatchParams bp) {
   __shared__ Smem<BS> sm;
   __shared__ int s_k;
   smem_clear<BS>(sm);
-  for (int j = bp.cta_off[blockIdx.x]; j < bp.cta_off[blockIdx.x + 1]; ++j) {
-    const int4 jb = bp.jobs[j];
-    color_graph<BS>(bp.params[jb.x], sm, Team{jb.y, jb.z});
-  }
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_k = atomicAdd(bp.solo_next, 1);
-    __syncthreads();
-    const int k = s_k;
-    if (k >= bp.nsolo) break;
-    color_graph<BS>(bp.params[bp.solo_list[k]], sm, Team{0, 1});
-  }
+  batched_jobs<BS, false>(bp, sm, &s_k);
 }
 
-cudaError_t occupancy_batched(int bs, int* blocks_per_sm) {
+// The pushing instantiation keeps 3 CTAs of 256 per SM (80 registers), as the
+// single-graph pushing kernel does.
+constexpr int batched_push_min_blocks(int bs) { return bs >= 512 ? 2 : 3; }
+
+template <int BS>
+__global__ void __launch_bounds__(BS, batched_push_min_blocks(BS)) batched_push_kernel(BatchParams bp) {
+  __shared__ Smem<BS> sm;
+  __shared__ int s_k;
+  smem_clear<BS>(sm);
+  batched_jobs<BS, true>(bp, sm, &s_k);
+}
+
+cudaError_t occupancy_batched(int bs, int* blocks_per_sm, bool push) {
   return with_block(bs, [&](auto B) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, batched_kernel<decltype(B)::value>, decltype(B)::value, 0);
+    return push ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      blocks_per_sm, batched_push_kernel<decltype(B)::value>, decltype(B)::value, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                      blocks_per_sm, batched_kernel<decltype(B)::value>, decltype(B)::value, 0);
   });
 }
 
 cudaError_t launch_batched(const BatchParams& bp, int bs, int blocks, bool cooperative,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool push) {
   return with_block(bs, [&](auto B) {
     BatchParams q = bp;
+    const void* k = push ? (const void*)batched_push_kernel<decltype(B)::value>
+                         : (const void*)batched_kernel<decltype(B)::value>;
     if (!cooperative) {
-      batched_kernel<decltype(B)::value><<<blocks, decltype(B)::value, 0, s>>>(q);
+      if (push)
+        batched_push_kernel<decltype(B)::value><<<blocks, decltype(B)::value, 0, s>>>(q);
+      else
+        batched_kernel<decltype(B)::value><<<blocks, decltype(B)::value, 0, s>>>(q);
       return cudaGetLastError();
     }
     void* args[] = {&q};
-    return cudaLaunchCooperativeKernel((const void*)batched_kernel<decltype(B)::value>,
-                                       dim3(blocks), dim3(decltype(B)::value), args, 0, s);
+    return cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(decltype(B)::value), args, 0, s);
   });
 }
 
@@ -161,9 +199,10 @@ void build_schedule(const Params* h_params, int32_t G, int grid, int max_team,
 
 cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid, bool cooperative,
                             const std::vector<int32_t>& lists, int32_t njobs, int32_t nsolo,
-                            Params* d_params, int32_t* d_lists, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyAsync(d_params, h_params, sizeof(Params) * (size_t)G,
-                                  cudaMemcpyHostToDevice, s);
+                            Params* d_params, int32_t* d_lists, cudaStream_t s, bool push) {
+  cudaError_t e = h_params ? cudaMemcpyAsync(d_params, h_params, sizeof(Params) * (size_t)G,
+                                             cudaMemcpyHostToDevice, s)
+                           : cudaSuccess;  // (already on the device)
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_lists, lists.data(), sizeof(int32_t) * lists.size(),
                         cudaMemcpyHostToDevice, s);
@@ -175,7 +214,7 @@ cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid,
   bp.solo_list = bp.cta_off + grid + 1;
   bp.nsolo = nsolo;
   bp.solo_next = d_lists + 4 * (size_t)njobs + grid + 1 + nsolo;
-  return launch_batched(bp, bs, grid, cooperative, s);
+  return launch_batched(bp, bs, grid, cooperative, s, push);
 }
 
 cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int max_team,
@@ -190,7 +229,7 @@ cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int g
     return cudaSuccess;
   }
   return launch_schedule(h_params, G, bs, grid, cooperative, lists, njobs, nsolo, d_params,
-                         d_lists, s);
+                         d_lists, s, false);
 }
 
 }  // namespace ipgc
@@ -213,7 +252,8 @@ struct BatchWs {
   size_t h_ctrl_cap = 0;
   int* h_err = nullptr;  // pinned
   std::vector<Params> params;
-  std::vector<int32_t> lists;
+  std::vector<int32_t> lists;   // schedule of the rescanning kernel
+  std::vector<int32_t> plists;  // ... of the pushing kernel
 };
 
 // workspace kept per context (one batch at a time per context)
@@ -300,16 +340,25 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   if (!W) return IPGC_ERR_OOM;
   const int t1 = ipgc::effective_t1(o.base), chunk = ipgc::effective_chunk(o.base);
   const int bs = o.base.block_size ? o.base.block_size : ipgc::kBlock;
+  if (o.base.forbidden < IPGC_FORBIDDEN_AUTO || o.base.forbidden > IPGC_FORBIDDEN_PUSH)
+    return IPGC_ERR_INVALID;
+  // forbidden-colour bitmaps unless rescanning is asked for
+  const bool push = o.base.forbidden != IPGC_FORBIDDEN_RESCAN;
 
   // per-graph slices of the workspace
-  std::vector<int64_t> item_base(num_graphs + 1), gbase(num_graphs + 1);
-  item_base[0] = gbase[0] = 0;
+  std::vector<int64_t> item_base(num_graphs + 1), gbase(num_graphs + 1), pq_base(num_graphs + 1),
+      lbase(num_graphs + 1);
+  item_base[0] = gbase[0] = pq_base[0] = lbase[0] = 0;
   for (int32_t g = 0; g < num_graphs; ++g) {
     const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
     int64_t nbig = e / (t1 + 1);
     if (nbig > n) nbig = n;
     item_base[g + 1] = item_base[g] + e / chunk + nbig + 1;
     gbase[g + 1] = gbase[g] + e / ((int64_t)chunk + 1) + 1;
+    pq_base[g + 1] = pq_base[g] + (push ? e / ipgc::kPushChunk + nbig + 1 : 0);
+    // lists are read as int4 windows from their buffer's base: every graph's
+    // slice starts on a 16-byte boundary
+    lbase[g + 1] = lbase[g] + (push ? (e + 3) / 4 * 4 : 0);
   }
   // the schedule needs only the shapes, so it is built first and sizes its buffer
   W->params.assign(num_graphs, Params());
@@ -317,20 +366,39 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     W->params[g].n = (int32_t)(node_off[g + 1] - node_off[g]);
     W->params[g].nnz = edge_off[g + 1] - edge_off[g];
   }
-  int occ = 0;
+  // one schedule per kernel, each for its own grid (occupancies differ): the
+  // pushing kernel first, then the rescanning one, which colours only the
+  // graphs the first left to it (or every graph, without pushing)
+  int occ = 0, pocc = 0;
   BCUDA(ipgc::occupancy_batched(bs, &occ));
-  const int grid = occ * ipgc::ctx_num_sms(ctx);
-  int32_t njobs = 0, nsolo = 0;
+  if (push) BCUDA(ipgc::occupancy_batched(bs, &pocc, true));
+  const int grid = occ * ipgc::ctx_num_sms(ctx), pgrid = pocc * ipgc::ctx_num_sms(ctx);
+  int32_t njobs = 0, nsolo = 0, pnjobs = 0, pnsolo = 0;
   ipgc::build_schedule(W->params.data(), num_graphs, grid, o.max_team, o.nnz_per_cta, W->lists,
                        &njobs, &nsolo, nullptr);
+  W->plists.clear();
+  if (push)
+    ipgc::build_schedule(W->params.data(), num_graphs, pgrid, o.max_team, o.nnz_per_cta,
+                         W->plists, &pnjobs, &pnsolo, nullptr);
   const size_t b_params = al256(sizeof(Params) * (size_t)num_graphs);
   const size_t b_lists = al256(sizeof(int32_t) * W->lists.size());
+  const size_t b_plists = al256(sizeof(int32_t) * W->plists.size());
   const size_t b_ctrl = al256(sizeof(Ctrl) * (size_t)num_graphs);
   const size_t b_node = al256(sizeof(int32_t) * (size_t)total_n);
   const size_t b_items = al256(sizeof(int4) * (size_t)item_base[num_graphs]);
   const size_t b_gbits = al256(sizeof(uint32_t) * ipgc::kGWords * (size_t)gbase[num_graphs]);
   const size_t b_gint = al256(sizeof(int32_t) * (size_t)gbase[num_graphs]);
-  const size_t need = b_params + b_lists + b_ctrl + 3 * b_node + 3 * b_items + b_gbits + 3 * b_gint + 256;
+  // pushing: bitmaps and two list buffers [entries], list counts (int2) x 2 and
+  // state, dead counts [slots], push queues, winners [nodes]
+  const size_t b_edge = push ? al256(sizeof(int32_t) * (size_t)total_e) : 0;
+  const size_t b_lists_e = push ? al256(sizeof(int32_t) * (size_t)lbase[num_graphs]) : 0;
+  const size_t b_gint2 = push ? al256(sizeof(int2) * (size_t)gbase[num_graphs]) : 0;
+  const size_t b_gpint = push ? b_gint : 0;
+  const size_t b_pq = al256(sizeof(int4) * (size_t)pq_base[num_graphs]);
+  const size_t b_pw = push ? b_node : 0;
+  const size_t need = b_params + b_lists + b_plists + b_ctrl + 3 * b_node + 3 * b_items + b_gbits +
+                      3 * b_gint + b_edge + 2 * b_lists_e + 2 * b_gint2 + 2 * b_gpint + b_pq +
+                      b_pw + 256;
   if (W->dev_bytes < need || W->device != dev) {
     if (W->dev) cudaFree(W->dev);
     W->dev = nullptr;
@@ -352,6 +420,8 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   w += b_params;
   int32_t* d_lists = (int32_t*)w;
   w += b_lists;
+  int32_t* d_plists = (int32_t*)w;
+  w += b_plists;
   Ctrl* d_ctrl = (Ctrl*)w;
   w += b_ctrl;
   int32_t* d_tent = (int32_t*)w;
@@ -374,6 +444,24 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   w += b_gint;
   int32_t* d_flag = (int32_t*)w;
   w += b_gint;
+  uint32_t* d_pbits = (uint32_t*)w;
+  w += b_edge;
+  int32_t* d_alist0 = (int32_t*)w;
+  w += b_lists_e;
+  int32_t* d_alist1 = (int32_t*)w;
+  w += b_lists_e;
+  int2* d_flen0 = (int2*)w;
+  w += b_gint2;
+  int2* d_flen1 = (int2*)w;
+  w += b_gint2;
+  int32_t* d_fst = (int32_t*)w;
+  w += b_gpint;
+  int32_t* d_fdead = (int32_t*)w;
+  w += b_gpint;
+  int4* d_pq = (int4*)w;
+  w += b_pq;
+  int32_t* d_pw = (int32_t*)w;
+  w += b_pw;
   int* d_err = (int*)w;
 
   // optional validation of every graph (one launch per graph)
@@ -423,11 +511,25 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     p.mlp = o.base.mode == IPGC_MODE_LEARNED ? d_mlp : nullptr;
     p.mlp_margin = o.base.policy_margin;
     p.col_vec = ((uintptr_t)p.col & 15u) == 0 ? 1 : 0;
+    if (push) {  // a graph's bitmaps and lists live inside its own entry range
+      p.pbits = d_pbits + edge_off[g];
+      p.alist[0] = d_alist0 + lbase[g];
+      p.alist[1] = d_alist1 + lbase[g];
+      p.flen[0] = d_flen0 + gbase[g];
+      p.flen[1] = d_flen1 + gbase[g];
+      p.fst = d_fst + gbase[g];
+      p.fdead = d_fdead + gbase[g];
+      p.pq = d_pq + pq_base[g];
+      p.pw = d_pw + node_off[g];
+    }
   }
 
   BCUDA(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl) * (size_t)num_graphs, s));
-  BCUDA(ipgc::launch_schedule(W->params.data(), num_graphs, bs, grid, true, W->lists, njobs, nsolo,
-                              d_params, d_lists, s));
+  if (push)
+    BCUDA(ipgc::launch_schedule(W->params.data(), num_graphs, bs, pgrid, true, W->plists, pnjobs,
+                                pnsolo, d_params, d_plists, s, true));
+  BCUDA(ipgc::launch_schedule(push ? nullptr : W->params.data(), num_graphs, bs, grid, true,
+                              W->lists, njobs, nsolo, d_params, d_lists, s));
 
   if (!per_graph_stats) return IPGC_OK;
   BCUDA(cudaMemcpyAsync(W->h_ctrl, d_ctrl, sizeof(Ctrl) * (size_t)num_graphs,

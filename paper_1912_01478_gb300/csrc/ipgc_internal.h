@@ -38,16 +38,18 @@ cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int32_t n
                             int* d_err, int blocks, cudaStream_t s);
 
 // Batched colouring (ipgc_batched.cu).
-cudaError_t occupancy_batched(int bs, int* blocks_per_sm);
+cudaError_t occupancy_batched(int bs, int* blocks_per_sm, bool push = false);
 // Schedule of a batch on `grid` CTAs (int32 lists, see build_schedule), then
 // its upload and launch; lists_cap bounds the device list buffer (rc =
 // IPGC_ERR_UNSUPPORTED when the schedule does not fit).
 void build_schedule(const Params* h_params, int32_t G, int grid, int max_team,
                     int64_t nnz_per_cta, std::vector<int32_t>& lists, int32_t* njobs_out,
                     int32_t* nsolo_out, int32_t* seq_out);
+// Uploads the parameters (unless h_params is null: already there) and the
+// lists, then launches the batched kernel: the pushing one when `push`.
 cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid, bool cooperative,
                             const std::vector<int32_t>& lists, int32_t njobs, int32_t nsolo,
-                            Params* d_params, int32_t* d_lists, cudaStream_t s);
+                            Params* d_params, int32_t* d_lists, cudaStream_t s, bool push = false);
 cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int max_team,
                                 int64_t nnz_per_cta, bool cooperative, Params* d_params,
                                 int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,

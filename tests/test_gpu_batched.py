@@ -81,6 +81,12 @@ def mixed_batch():
         dict(mode="data"),
         dict(mode="topo", nnz_per_cta=20_000),
         dict(block_size=512, chunk=256, t1=8),
+        # rows rescanned every round (the default pushes into bitmaps)
+        dict(forbidden="rescan"),
+        dict(forbidden="rescan", nnz_per_cta=5_000, max_team=16),
+        dict(forbidden="rescan", mode="topo", nnz_per_cta=20_000),
+        # small t1: most graphs keep bitmaps; big chunk: few list items
+        dict(t1=4, chunk=4096, nnz_per_cta=5_000),
     ],
 )
 def test_batch_matches_oracle(ctx, mixed_batch, kw):
