@@ -428,7 +428,9 @@ IPGC_API int ipgc_policy_load(ipgc_ctx* ctx, const float* w, int32_t len);
  * NULL) its time. ipgc_autotune times ipgc_color_ex on the given graph
  * (colors_scratch: device int32[n], overwritten); ipgc_batched_autotune times
  * ipgc_color_batched on the batch's first sample_graphs graphs (0 = all),
- * writing their colours to colors_cat. Errors as the timed calls.
+ * then (with a sample) its choice and the given options on the whole batch,
+ * keeping the faster, writing colours to colors_cat. Errors as the timed
+ * calls.
  */
 IPGC_API int ipgc_autotune(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
                            int64_t nnz, int32_t* colors_scratch, int32_t reps, ipgc_options* opt,

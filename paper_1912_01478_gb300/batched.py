@@ -72,8 +72,10 @@ def plan(n, nnz, grid: int, max_team: int = 0, nnz_per_cta: int = 131072):
 
 
 def describe(o: BatchOptions) -> dict:
+    forbidden = {v: k for k, v in ipgc.FORBIDDEN.items()}.get(o.base.forbidden, o.base.forbidden)
     return dict(t1=o.base.t1, chunk=o.base.chunk, block_size=o.base.block_size,
-                max_team=o.max_team, nnz_per_cta=int(o.nnz_per_cta), mode=o.base.mode)
+                max_team=o.max_team, nnz_per_cta=int(o.nnz_per_cta), mode=o.base.mode,
+                forbidden=forbidden)
 
 _bound = False
 

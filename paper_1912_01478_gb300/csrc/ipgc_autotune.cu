@@ -1,13 +1,15 @@
 // Schedule autotuner for the single-graph and batched colourings.
 //
-// The schedule (degree split t1, work-item size, CTA size, team size and the
-// size from which a graph of a batch gets a team) changes only speed, never a
-// colour, so it can be chosen by measurement. The tuner runs a coordinate
+// The schedule (degree split t1, work-item size, CTA size, team size, the
+// size from which a graph of a batch gets a team, and for batches whether
+// forbidden colours are pushed into bitmaps or rows rescanned) changes only
+// speed, never a colour, so it can be chosen by measurement. The tuner runs a coordinate
 // descent from the caller's options: for each knob in turn it times every
 // candidate value with the others fixed (best of `reps` launches, CUDA events
 // on the caller's stream) and keeps the fastest. The batched tuner times the
 // batch's first `sample_graphs` graphs, a contiguous prefix that is itself a
-// valid batch.
+// valid batch, then times its choice and the caller's options on the whole
+// batch and keeps the faster (a prefix need not pack like the whole batch).
 #include <cfloat>
 #include <cstring>
 #include <vector>
@@ -125,6 +127,8 @@ int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node
   const int validate = base.base.validate;
   base.base.validate = 0;
   std::vector<Knob<ipgc_batch_options>> knobs = {
+      {[](ipgc_batch_options& o, int64_t v) { o.base.forbidden = (int32_t)v; },
+       {IPGC_FORBIDDEN_AUTO, IPGC_FORBIDDEN_RESCAN}},
       {[](ipgc_batch_options& o, int64_t v) { o.base.chunk = (int32_t)v; }, {512, 1024, 2048}},
       {[](ipgc_batch_options& o, int64_t v) { o.base.t1 = (int32_t)v; }, {16, 32, 64, 128, 255}},
       {[](ipgc_batch_options& o, int64_t v) { o.nnz_per_cta = v; },
@@ -132,7 +136,8 @@ int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node
       {[](ipgc_batch_options& o, int64_t v) { o.max_team = (int32_t)v; }, {0, 4, 16, 64}},
       {[](ipgc_batch_options& o, int64_t v) { o.base.block_size = (int32_t)v; }, {256, 512}},
   };
-  const int rc = descend(
+  const ipgc_batch_options start = base;
+  int rc = descend(
       &base, knobs,
       [&](const ipgc_batch_options& o) {
         return ipgc_color_batched(ctx, G, node_off, edge_off, rowptr_cat, col_cat, colors_cat,
@@ -140,6 +145,20 @@ int ipgc_batched_autotune(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node
       },
       s, reps, best_ms);
   if (rc != IPGC_OK) return rc;
+  if (G < num_graphs) {  // the choice against the caller's options, on every graph
+    float t_tuned = 0, t_start = 0;
+    auto whole = [&](const ipgc_batch_options& o) {
+      return [&, o] {
+        return ipgc_color_batched(ctx, num_graphs, node_off, edge_off, rowptr_cat, col_cat,
+                                  colors_cat, nullptr, &o, stream);
+      };
+    };
+    rc = time_best(whole(base), s, reps, &t_tuned);
+    if (rc == IPGC_OK) rc = time_best(whole(start), s, reps, &t_start);
+    if (rc != IPGC_OK) return rc;
+    if (t_start < t_tuned) base = start;
+    if (best_ms) *best_ms = t_start < t_tuned ? t_start : t_tuned;
+  }
   base.base.validate = validate;
   *opt = base;
   return IPGC_OK;
