@@ -1,7 +1,8 @@
 """Seeded synthetic graph generators (inputs only; no colouring arithmetic).
 
 Thin ctypes binding over ``libgraphgen.so`` (built from ``graphgen.c`` beside
-this file by :func:`build`). Every graph is undirected, symmetric, has no
+this file by :func:`build`; its C ABI is declared in
+``include/ipgc_graphgen.h``). Every graph is undirected, symmetric, has no
 self-loops or duplicate edges and sorted CSR rows, matching the preprocessing
 the paper applies to its inputs (Section V). Arrays come back as numpy int32
 (rowptr, col) or int64 (batch offsets).
@@ -22,6 +23,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "graphgen.c")
 _LIB = os.path.join(_HERE, "libgraphgen.so")
+_HEADER = os.path.join(os.path.dirname(os.path.dirname(_HERE)), "include", "ipgc_graphgen.h")
 _lock = threading.Lock()
 _lib = None
 
@@ -52,10 +54,11 @@ def build(force: bool = False) -> str:
     """Compile libgraphgen.so with gcc (OpenMP over graphs of a batch)."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "graphgen.h"))
+            os.path.getmtime(_SRC), os.path.getmtime(_HEADER)
         ):
             tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fvisibility=hidden",
+                   "-I", os.path.dirname(_HEADER), "-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB)
     return _LIB
@@ -69,23 +72,23 @@ def _load():
     lib = ctypes.CDLL(_LIB)
     P = ctypes.POINTER
     i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
-    lib.gg_er.argtypes = [u64, i32, i64, P(_Csr)]
-    lib.gg_rmat.argtypes = [u64, i32, i64, dbl, dbl, dbl, i32, i32, P(_Csr)]
-    lib.gg_road.argtypes = [u64, i32, dbl, dbl, P(_Csr)]
-    lib.gg_from_edges.argtypes = [i32, i64, P(i32), P(i32), P(_Csr)]
-    lib.gg_rgg.argtypes = [u64, i32, i32, dbl, P(_Csr)]
-    lib.gg_lattice3.argtypes = [i32, i32, P(_Csr)]
-    lib.gg_hubs.argtypes = [u64, i32, i64, i32, i64, dbl, P(_Csr)]
-    lib.gg_batch.argtypes = [u64, i32, i32, i32, dbl, dbl, i32, dbl, dbl, dbl, P(_Batch)]
-    lib.gg_free_csr.argtypes = [P(_Csr)]
-    lib.gg_free_batch.argtypes = [P(_Batch)]
-    lib.gg_hash_words.argtypes = [P(i32), i64, u64]
-    lib.gg_hash_words.restype = u64
-    lib.gg_derive_seed.argtypes = [u64, u64]
-    lib.gg_derive_seed.restype = u64
-    lib.gg_num_threads.restype = ctypes.c_int
-    for f in (lib.gg_er, lib.gg_rmat, lib.gg_road, lib.gg_from_edges, lib.gg_batch, lib.gg_rgg,
-              lib.gg_lattice3, lib.gg_hubs):
+    lib.ipgc_gen_er.argtypes = [u64, i32, i64, P(_Csr)]
+    lib.ipgc_gen_rmat.argtypes = [u64, i32, i64, dbl, dbl, dbl, i32, i32, P(_Csr)]
+    lib.ipgc_gen_road.argtypes = [u64, i32, dbl, dbl, P(_Csr)]
+    lib.ipgc_gen_from_edges.argtypes = [i32, i64, P(i32), P(i32), P(_Csr)]
+    lib.ipgc_gen_rgg.argtypes = [u64, i32, i32, dbl, P(_Csr)]
+    lib.ipgc_gen_lattice3.argtypes = [i32, i32, P(_Csr)]
+    lib.ipgc_gen_hubs.argtypes = [u64, i32, i64, i32, i64, dbl, P(_Csr)]
+    lib.ipgc_gen_batch.argtypes = [u64, i32, i32, i32, dbl, dbl, i32, dbl, dbl, dbl, P(_Batch)]
+    lib.ipgc_gen_free_csr.argtypes = [P(_Csr)]
+    lib.ipgc_gen_free_batch.argtypes = [P(_Batch)]
+    lib.ipgc_gen_hash_words.argtypes = [P(i32), i64, u64]
+    lib.ipgc_gen_hash_words.restype = u64
+    lib.ipgc_gen_derive_seed.argtypes = [u64, u64]
+    lib.ipgc_gen_derive_seed.restype = u64
+    lib.ipgc_gen_num_threads.restype = ctypes.c_int
+    for f in (lib.ipgc_gen_er, lib.ipgc_gen_rmat, lib.ipgc_gen_road, lib.ipgc_gen_from_edges,
+              lib.ipgc_gen_batch, lib.ipgc_gen_rgg, lib.ipgc_gen_lattice3, lib.ipgc_gen_hubs):
         f.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -98,7 +101,7 @@ def _take(c: _Csr):
     col = (
         np.ctypeslib.as_array(c.col, shape=(nnz,)).copy() if nnz > 0 else np.zeros(0, np.int32)
     )
-    lib.gg_free_csr(ctypes.byref(c))
+    lib.ipgc_gen_free_csr(ctypes.byref(c))
     return rowptr, col
 
 
@@ -110,7 +113,7 @@ def _check(rc: int, what: str):
 def er(n: int, m: int, seed: int):
     """Erdos-Renyi G(n, m) with exactly m undirected edges. Returns (rowptr, col)."""
     c = _Csr()
-    _check(_load().gg_er(seed, n, m, ctypes.byref(c)), "er")
+    _check(_load().ipgc_gen_er(seed, n, m, ctypes.byref(c)), "er")
     return _take(c)
 
 
@@ -120,7 +123,8 @@ def rmat(scale: int, edge_factor: int, seed: int, abc=RMAT_ABC, n_limit: int = 0
     c = _Csr()
     nedges = int(edge_factor) * (n_limit if n_limit > 0 else (1 << scale))
     _check(
-        _load().gg_rmat(seed, scale, nedges, a, b, cc, n_limit, 1 if permute else 0, ctypes.byref(c)),
+        _load().ipgc_gen_rmat(seed, scale, nedges, a, b, cc, n_limit, 1 if permute else 0,
+                              ctypes.byref(c)),
         "rmat",
     )
     return _take(c)
@@ -129,7 +133,7 @@ def rmat(scale: int, edge_factor: int, seed: int, abc=RMAT_ABC, n_limit: int = 0
 def road(side: int, seed: int, p_delete: float = 0.30, frac_long: float = 0.01):
     """side x side grid, p_delete of edges removed, frac_long long-range edges added."""
     c = _Csr()
-    _check(_load().gg_road(seed, side, p_delete, frac_long, ctypes.byref(c)), "road")
+    _check(_load().ipgc_gen_road(seed, side, p_delete, frac_long, ctypes.byref(c)), "road")
     return _take(c)
 
 
@@ -137,7 +141,7 @@ def rgg(n: int, dim: int, avg_degree: float, seed: int):
     """Random geometric graph in the unit square (dim 2) or cube (dim 3), mean
     degree avg_degree away from the border, IDs in grid-cell order."""
     c = _Csr()
-    _check(_load().gg_rgg(seed, n, dim, avg_degree, ctypes.byref(c)), "rgg")
+    _check(_load().ipgc_gen_rgg(seed, n, dim, avg_degree, ctypes.byref(c)), "rgg")
     return _take(c)
 
 
@@ -145,14 +149,14 @@ def lattice3(side: int, r2: int):
     """side^3 lattice, edges between nodes at squared distance <= r2 (r2 = 6:
     80 neighbours inside)."""
     c = _Csr()
-    _check(_load().gg_lattice3(side, r2, ctypes.byref(c)), "lattice3")
+    _check(_load().ipgc_gen_lattice3(side, r2, ctypes.byref(c)), "lattice3")
     return _take(c)
 
 
 def hubs(n: int, m_base: int, nhubs: int, max_deg: int, alpha: float, seed: int):
     """Uniform base of m_base pairs plus nhubs hubs of degree max_deg / (h+1)^alpha."""
     c = _Csr()
-    _check(_load().gg_hubs(seed, n, m_base, nhubs, max_deg, alpha, ctypes.byref(c)), "hubs")
+    _check(_load().ipgc_gen_hubs(seed, n, m_base, nhubs, max_deg, alpha, ctypes.byref(c)), "hubs")
     return _take(c)
 
 
@@ -164,7 +168,7 @@ def from_edges(n: int, src, dst):
     c = _Csr()
     P = ctypes.POINTER(ctypes.c_int32)
     _check(
-        _load().gg_from_edges(
+        _load().ipgc_gen_from_edges(
             n, src.size, src.ctypes.data_as(P), dst.ctypes.data_as(P), ctypes.byref(c)
         ),
         "from_edges",
@@ -187,7 +191,8 @@ def batch(
     a, bb, c = abc
     lib = _load()
     _check(
-        lib.gg_batch(seed, num_graphs, nmin, nmax, deg_lo, deg_hi, rmat_ef, a, bb, c, ctypes.byref(b)),
+        lib.ipgc_gen_batch(seed, num_graphs, nmin, nmax, deg_lo, deg_hi, rmat_ef, a, bb, c,
+                           ctypes.byref(b)),
         "batch",
     )
     G = int(b.num_graphs)
@@ -199,7 +204,7 @@ def batch(
     col_cat = (
         np.ctypeslib.as_array(b.col_cat, shape=(ncol,)).copy() if ncol > 0 else np.zeros(0, np.int32)
     )
-    lib.gg_free_batch(ctypes.byref(b))
+    lib.ipgc_gen_free_batch(ctypes.byref(b))
     return dict(node_off=node_off, edge_off=edge_off, rowptr_cat=rowptr_cat, col_cat=col_cat)
 
 
@@ -218,16 +223,16 @@ def graph_hash(rowptr, col) -> int:
     P = ctypes.POINTER(ctypes.c_int32)
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     cl = np.ascontiguousarray(col, dtype=np.int32)
-    h = lib.gg_hash_words(rp.ctypes.data_as(P), rp.size, 0)
-    return int(lib.gg_hash_words(cl.ctypes.data_as(P), cl.size, h))
+    h = lib.ipgc_gen_hash_words(rp.ctypes.data_as(P), rp.size, 0)
+    return int(lib.ipgc_gen_hash_words(cl.ctypes.data_as(P), cl.size, h))
 
 
 def derive_seed(seed: int, index: int) -> int:
-    return int(_load().gg_derive_seed(seed, index))
+    return int(_load().ipgc_gen_derive_seed(seed, index))
 
 
 def num_threads() -> int:
-    return int(_load().gg_num_threads())
+    return int(_load().ipgc_gen_num_threads())
 
 
 def batch_workload(num_graphs: int = 4096, seed: int = 4):

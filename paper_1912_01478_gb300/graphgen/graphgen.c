@@ -16,10 +16,11 @@
  * 53 bits. All arithmetic is integer or IEEE double, so the output is the same
  * on x86-64 and aarch64.
  *
- * Memory returned through gg_csr / gg_batch is malloc()ed here and released
- * with gg_free_csr / gg_free_batch.
+ * Memory returned through ipgc_gen_csr / ipgc_gen_batch_t is malloc()ed
+ * here and released with ipgc_gen_free_csr / ipgc_gen_free_batch. The C ABI
+ * is declared in include/ipgc_graphgen.h.
  */
-#include "graphgen.h"
+#include "ipgc_graphgen.h"
 
 #include <math.h>
 #include <stdlib.h>
@@ -68,7 +69,7 @@ static inline uint64_t rng_below(rng_t* r, uint64_t k) {
 
 static inline double rng_unit(rng_t* r) { return (double)(rng_u64(r) >> 11) * 0x1.0p-53; }
 
-uint64_t gg_derive_seed(uint64_t seed, uint64_t index) {
+uint64_t ipgc_gen_derive_seed(uint64_t seed, uint64_t index) {
   uint64_t x = seed ^ (0xd1b54a32d192ed03ULL * (index + 1));
   splitmix64(&x);
   return splitmix64(&x);
@@ -105,7 +106,7 @@ static void sort_run(int32_t* p, int64_t len) {
  * adjacent duplicates and compact. The result does not depend on the order
  * of the scatter, so the passes may run on several host threads.
  */
-static int build_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, gg_csr* out) {
+static int build_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, ipgc_gen_csr* out) {
   memset(out, 0, sizeof(*out));
   out->n = n;
   int64_t* start = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
@@ -115,7 +116,7 @@ static int build_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
     free(start);
     free(pos);
     free(rowptr);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
 #pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < m; ++e) {
@@ -133,7 +134,7 @@ static int build_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
     free(start);
     free(pos);
     free(rowptr);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
   memcpy(pos, start, ((size_t)n + 1) * sizeof(int64_t));
 #pragma omp parallel for schedule(static)
@@ -170,7 +171,7 @@ static int build_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
     free(pos);
     free(rowptr);
     free(col);
-    return GG_ERR_TOO_BIG;
+    return IPGC_GEN_ERR_TOO_BIG;
   }
   rowptr[n] = (int32_t)acc;
   /* compact rows towards the front (destination never overtakes source) */
@@ -183,13 +184,14 @@ static int build_csr(int32_t n, int64_t m, const int32_t* src, const int32_t* ds
   out->rowptr = rowptr;
   out->col = shrunk ? shrunk : col;
   out->nnz = acc;
-  return GG_OK;
+  return IPGC_GEN_OK;
 }
 
-int gg_from_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, gg_csr* out) {
-  if (n < 0 || m < 0 || !out) return GG_ERR_ARG;
+int ipgc_gen_from_edges(int32_t n, int64_t m, const int32_t* src, const int32_t* dst, ipgc_gen_csr* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
+  if (n < 0 || m < 0 || !out) return IPGC_GEN_ERR_ARG;
   for (int64_t e = 0; e < m; ++e)
-    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return GG_ERR_ARG;
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return IPGC_GEN_ERR_ARG;
   return build_csr(n, m, src, dst, out);
 }
 
@@ -204,7 +206,7 @@ static int er_edges(rng_t* r, int32_t n, int64_t m, int32_t* src, int32_t* dst) 
   uint64_t cap = 16;
   while (cap < (uint64_t)m * 2 + 16) cap <<= 1;
   uint64_t* tab = (uint64_t*)malloc(cap * sizeof(uint64_t));
-  if (!tab) return GG_ERR_OOM;
+  if (!tab) return IPGC_GEN_ERR_OOM;
   memset(tab, 0xff, cap * sizeof(uint64_t));
   const uint64_t EMPTY = ~0ULL;
   for (int64_t e = 0; e < m;) {
@@ -229,13 +231,14 @@ static int er_edges(rng_t* r, int32_t n, int64_t m, int32_t* src, int32_t* dst) 
     ++e;
   }
   free(tab);
-  return GG_OK;
+  return IPGC_GEN_OK;
 }
 
-int gg_er(uint64_t seed, int32_t n, int64_t m, gg_csr* out) {
-  if (!out || n < 0 || m < 0) return GG_ERR_ARG;
-  if (n < 2 && m > 0) return GG_ERR_ARG;
-  if ((double)m > 0.5 * (double)n * (double)(n - 1)) return GG_ERR_ARG;
+int ipgc_gen_er(uint64_t seed, int32_t n, int64_t m, ipgc_gen_csr* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
+  if (!out || n < 0 || m < 0) return IPGC_GEN_ERR_ARG;
+  if (n < 2 && m > 0) return IPGC_GEN_ERR_ARG;
+  if ((double)m > 0.5 * (double)n * (double)(n - 1)) return IPGC_GEN_ERR_ARG;
   rng_t r;
   rng_seed(&r, seed);
   int32_t* src = (int32_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
@@ -243,10 +246,10 @@ int gg_er(uint64_t seed, int32_t n, int64_t m, gg_csr* out) {
   if (!src || !dst) {
     free(src);
     free(dst);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
   int rc = er_edges(&r, n, m, src, dst);
-  if (rc == GG_OK) rc = build_csr(n, m, src, dst, out);
+  if (rc == IPGC_GEN_OK) rc = build_csr(n, m, src, dst, out);
   free(src);
   free(dst);
   return rc;
@@ -295,10 +298,11 @@ static int32_t* fisher_yates(rng_t* r, int32_t n) {
  * endpoint >= n_limit is redrawn whole. With permute != 0 the node IDs are
  * relabelled by a Fisher-Yates permutation drawn after the edges.
  */
-int gg_rmat(uint64_t seed, int32_t scale, int64_t nedges, double a, double b, double c,
-            int32_t n_limit, int32_t permute, gg_csr* out) {
-  if (!out || scale < 0 || scale > 30 || nedges < 0) return GG_ERR_ARG;
-  if (a < 0 || b < 0 || c < 0 || a + b + c > 1.0) return GG_ERR_ARG;
+int ipgc_gen_rmat(uint64_t seed, int32_t scale, int64_t nedges, double a, double b, double c,
+            int32_t n_limit, int32_t permute, ipgc_gen_csr* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
+  if (!out || scale < 0 || scale > 30 || nedges < 0) return IPGC_GEN_ERR_ARG;
+  if (a < 0 || b < 0 || c < 0 || a + b + c > 1.0) return IPGC_GEN_ERR_ARG;
   int32_t full = (int32_t)1 << scale;
   int32_t n = (n_limit > 0 && n_limit < full) ? n_limit : full;
   rng_t r; /* main stream: only the permutation */
@@ -308,7 +312,7 @@ int gg_rmat(uint64_t seed, int32_t scale, int64_t nedges, double a, double b, do
   if (!src || !dst) {
     free(src);
     free(dst);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
   const double two53 = 9007199254740992.0;
   const uint64_t A = (uint64_t)(a * two53), AB = (uint64_t)((a + b) * two53),
@@ -319,7 +323,7 @@ int gg_rmat(uint64_t seed, int32_t scale, int64_t nedges, double a, double b, do
 #pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < nch; ++k) {
     rng_t cr;
-    rng_seed(&cr, gg_derive_seed(seed, (uint64_t)k));
+    rng_seed(&cr, ipgc_gen_derive_seed(seed, (uint64_t)k));
     int64_t e1 = (k + 1) * CH < nedges ? (k + 1) * CH : nedges;
     for (int64_t e = k * CH; e < e1; ++e) {
       int32_t u, v;
@@ -335,7 +339,7 @@ int gg_rmat(uint64_t seed, int32_t scale, int64_t nedges, double a, double b, do
     if (!p) {
       free(src);
       free(dst);
-      return GG_ERR_OOM;
+      return IPGC_GEN_ERR_OOM;
     }
     for (int64_t e = 0; e < nedges; ++e) {
       src[e] = p[src[e]];
@@ -357,9 +361,10 @@ int gg_rmat(uint64_t seed, int32_t scale, int64_t nedges, double a, double b, do
  * long-range edges with uniform endpoints (self-loops redrawn) are added.
  * Duplicates among the long-range edges are removed by the CSR build.
  */
-int gg_road(uint64_t seed, int32_t side, double p_delete, double frac_long, gg_csr* out) {
+int ipgc_gen_road(uint64_t seed, int32_t side, double p_delete, double frac_long, ipgc_gen_csr* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
   if (!out || side < 0 || side > 46340 || p_delete < 0 || p_delete > 1 || frac_long < 0)
-    return GG_ERR_ARG;
+    return IPGC_GEN_ERR_ARG;
   int32_t n = side * side;
   int64_t grid = side > 0 ? 2LL * side * (side - 1) : 0;
   int64_t cap = grid + (int64_t)(frac_long * (double)grid) + 16;
@@ -368,7 +373,7 @@ int gg_road(uint64_t seed, int32_t side, double p_delete, double frac_long, gg_c
   if (!src || !dst) {
     free(src);
     free(dst);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
   rng_t r;
   rng_seed(&r, seed);
@@ -414,8 +419,9 @@ int gg_road(uint64_t seed, int32_t side, double p_delete, double frac_long, gg_c
  * nearby IDs, as in the rgg graphs of the DIMACS collection. Coordinates come
  * from per-chunk streams (2^16 points per chunk).
  */
-int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out) {
-  if (!out || n < 0 || (dim != 2 && dim != 3) || !(avg_degree >= 0)) return GG_ERR_ARG;
+int ipgc_gen_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, ipgc_gen_csr* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
+  if (!out || n < 0 || (dim != 2 && dim != 3) || !(avg_degree >= 0)) return IPGC_GEN_ERR_ARG;
   const double pi = 3.14159265358979323846;
   const double r = dim == 2 ? sqrt(avg_degree / (pi * (n > 0 ? n : 1)))
                             : cbrt(3.0 * avg_degree / (4.0 * pi * (n > 0 ? n : 1)));
@@ -431,13 +437,13 @@ int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out
   int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1));
   if (!pt || !sp || !cell || !cstart || !cnt) {
     free(pt); free(sp); free(cell); free(cstart); free(cnt);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
   const int64_t chunk = 1 << 16, nch = ((int64_t)n + chunk - 1) / chunk;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t k = 0; k < nch; ++k) {
     rng_t rr;
-    rng_seed(&rr, gg_derive_seed(seed, (uint64_t)k));
+    rng_seed(&rr, ipgc_gen_derive_seed(seed, (uint64_t)k));
     const int64_t hi = (k + 1) * chunk < n ? (k + 1) * chunk : n;
     for (int64_t i = k * chunk; i < hi; ++i) {
       int64_t c = 0, mul = 1;
@@ -459,7 +465,7 @@ int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out
     int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
     if (!fill) {
       free(pt); free(sp); free(cell); free(cstart); free(cnt);
-      return GG_ERR_OOM;
+      return IPGC_GEN_ERR_OOM;
     }
     memcpy(fill, cstart, sizeof(int64_t) * (size_t)ncell);
     for (int64_t i = 0; i < n; ++i) {
@@ -481,7 +487,7 @@ int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out
       dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
       if (!src || !dst) {
         free(src); free(dst); free(sp); free(cell); free(cstart); free(cnt);
-        return GG_ERR_OOM;
+        return IPGC_GEN_ERR_OOM;
       }
     }
 #pragma omp parallel for schedule(dynamic, 4096)
@@ -526,7 +532,7 @@ int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out
       return rc;
     }
   }
-  return GG_ERR_ARG;  /* not reached */
+  return IPGC_GEN_ERR_ARG;  /* not reached */
 }
 
 /*
@@ -535,8 +541,9 @@ int gg_rgg(uint64_t seed, int32_t n, int32_t dim, double avg_degree, gg_csr* out
  * r2 = 6 gives 80 neighbours inside the lattice (fewer at the faces), the
  * degree profile of a regular 3-D finite-element mesh.
  */
-int gg_lattice3(int32_t side, int32_t r2, gg_csr* out) {
-  if (!out || side < 0 || side > 1290 || r2 < 1 || r2 > 16) return GG_ERR_ARG;
+int ipgc_gen_lattice3(int32_t side, int32_t r2, ipgc_gen_csr* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
+  if (!out || side < 0 || side > 1290 || r2 < 1 || r2 > 16) return IPGC_GEN_ERR_ARG;
   int off[400][3];
   int no = 0;
   const int R = (int)floor(sqrt((double)r2));
@@ -552,9 +559,9 @@ int gg_lattice3(int32_t side, int32_t r2, gg_csr* out) {
         ++no;
       }
   const int64_t n = (int64_t)side * side * side;
-  if (n > INT32_MAX) return GG_ERR_TOO_BIG;
+  if (n > INT32_MAX) return IPGC_GEN_ERR_TOO_BIG;
   int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
-  if (!cnt) return GG_ERR_OOM;
+  if (!cnt) return IPGC_GEN_ERR_OOM;
   for (int pass = 0; pass < 2; ++pass) {
     int32_t* src = NULL;
     int32_t* dst = NULL;
@@ -564,7 +571,7 @@ int gg_lattice3(int32_t side, int32_t r2, gg_csr* out) {
       dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
       if (!src || !dst) {
         free(src); free(dst); free(cnt);
-        return GG_ERR_OOM;
+        return IPGC_GEN_ERR_OOM;
       }
     }
 #pragma omp parallel for schedule(static)
@@ -592,7 +599,7 @@ int gg_lattice3(int32_t side, int32_t r2, gg_csr* out) {
       return rc;
     }
   }
-  return GG_ERR_ARG;  /* not reached */
+  return IPGC_GEN_ERR_ARG;  /* not reached */
 }
 
 /*
@@ -601,11 +608,12 @@ int gg_lattice3(int32_t side, int32_t r2, gg_csr* out) {
  * hub h (a uniform node) joined to round(max_deg / (h + 1)^alpha) uniform
  * nodes. Every stream is per chunk of 2^16 draws or per hub.
  */
-int gg_hubs(uint64_t seed, int32_t n, int64_t m_base, int32_t nhubs, int64_t max_deg, double alpha,
-            gg_csr* out) {
-  if (!out || n < 1 || m_base < 0 || nhubs < 0 || max_deg < 0 || !(alpha >= 0)) return GG_ERR_ARG;
+int ipgc_gen_hubs(uint64_t seed, int32_t n, int64_t m_base, int32_t nhubs, int64_t max_deg, double alpha,
+            ipgc_gen_csr* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
+  if (!out || n < 1 || m_base < 0 || nhubs < 0 || max_deg < 0 || !(alpha >= 0)) return IPGC_GEN_ERR_ARG;
   int64_t* hstart = (int64_t*)malloc(sizeof(int64_t) * ((size_t)nhubs + 1));
-  if (!hstart) return GG_ERR_OOM;
+  if (!hstart) return IPGC_GEN_ERR_OOM;
   hstart[0] = m_base;
   for (int32_t h = 0; h < nhubs; ++h) {
     int64_t d = (int64_t)llround((double)max_deg / pow((double)(h + 1), alpha));
@@ -617,13 +625,13 @@ int gg_hubs(uint64_t seed, int32_t n, int64_t m_base, int32_t nhubs, int64_t max
   int32_t* dst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
   if (!src || !dst) {
     free(src); free(dst); free(hstart);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
   const int64_t chunk = 1 << 16, nch = (m_base + chunk - 1) / chunk;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t k = 0; k < nch; ++k) {
     rng_t rr;
-    rng_seed(&rr, gg_derive_seed(seed, (uint64_t)k));
+    rng_seed(&rr, ipgc_gen_derive_seed(seed, (uint64_t)k));
     const int64_t hi = (k + 1) * chunk < m_base ? (k + 1) * chunk : m_base;
     for (int64_t e = k * chunk; e < hi; ++e) {
       src[e] = (int32_t)rng_below(&rr, (uint64_t)n);
@@ -633,7 +641,7 @@ int gg_hubs(uint64_t seed, int32_t n, int64_t m_base, int32_t nhubs, int64_t max
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t h = 0; h < nhubs; ++h) {
     rng_t rr;
-    rng_seed(&rr, gg_derive_seed(seed ^ 0x68756273ULL, (uint64_t)h));
+    rng_seed(&rr, ipgc_gen_derive_seed(seed ^ 0x68756273ULL, (uint64_t)h));
     const int32_t hub = (int32_t)rng_below(&rr, (uint64_t)n);
     for (int64_t e = hstart[h]; e < hstart[h + 1]; ++e) {
       src[e] = hub;
@@ -647,7 +655,7 @@ int gg_hubs(uint64_t seed, int32_t n, int64_t m_base, int32_t nhubs, int64_t max
   return rc;
 }
 
-void gg_free_csr(gg_csr* g) {
+void ipgc_gen_free_csr(ipgc_gen_csr* g) {
   if (!g) return;
   free(g->rowptr);
   free(g->col);
@@ -661,7 +669,7 @@ void gg_free_csr(gg_csr* g) {
 
 /*
  * A batch of independent graphs. Graph g draws its node count and parameters
- * from gg_derive_seed(seed, g), so each graph depends only on (seed, g) and
+ * from ipgc_gen_derive_seed(seed, g), so each graph depends only on (seed, g) and
  * the batch is the same whatever the number of host threads:
  *   n_g = floor(exp(U(ln nmin, ln(nmax + 1)))) clamped to [nmin, nmax]
  *   even g: Erdos-Renyi with average degree U(deg_lo, deg_hi), m = round(n d / 2)
@@ -672,19 +680,20 @@ void gg_free_csr(gg_csr* g) {
  * node_off[g] + g) and col_cat (graph g's local neighbour IDs start at
  * edge_off[g]).
  */
-int gg_batch(uint64_t seed, int32_t num_graphs, int32_t nmin, int32_t nmax, double deg_lo,
-             double deg_hi, int32_t rmat_ef, double a, double b, double c, gg_batch_t* out) {
+int ipgc_gen_batch(uint64_t seed, int32_t num_graphs, int32_t nmin, int32_t nmax, double deg_lo,
+             double deg_hi, int32_t rmat_ef, double a, double b, double c, ipgc_gen_batch_t* out) {
+  if (out) memset(out, 0, sizeof(*out)); /* no memory on any error */
   if (!out || num_graphs < 0 || nmin < 2 || nmax < nmin || deg_lo < 0 || deg_hi < deg_lo ||
       rmat_ef < 0)
-    return GG_ERR_ARG;
+    return IPGC_GEN_ERR_ARG;
   memset(out, 0, sizeof(*out));
-  gg_csr* gs = (gg_csr*)calloc((size_t)(num_graphs > 0 ? num_graphs : 1), sizeof(gg_csr));
-  if (!gs) return GG_ERR_OOM;
-  int failed = GG_OK;
+  ipgc_gen_csr* gs = (ipgc_gen_csr*)calloc((size_t)(num_graphs > 0 ? num_graphs : 1), sizeof(ipgc_gen_csr));
+  if (!gs) return IPGC_GEN_ERR_OOM;
+  int failed = IPGC_GEN_OK;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t g = 0; g < num_graphs; ++g) {
     rng_t r;
-    uint64_t gseed = gg_derive_seed(seed, (uint64_t)g);
+    uint64_t gseed = ipgc_gen_derive_seed(seed, (uint64_t)g);
     rng_seed(&r, gseed);
     double lo = log((double)nmin), hi = log((double)nmax + 1.0);
     int32_t ng = (int32_t)floor(exp(lo + (hi - lo) * rng_unit(&r)));
@@ -696,19 +705,19 @@ int gg_batch(uint64_t seed, int32_t num_graphs, int32_t nmin, int32_t nmax, doub
       int64_t m = (int64_t)llround((double)ng * d * 0.5);
       int64_t mmax = (int64_t)ng * (ng - 1) / 2;
       if (m > mmax) m = mmax;
-      rc = gg_er(rng_u64(&r), ng, m, &gs[g]);
+      rc = ipgc_gen_er(rng_u64(&r), ng, m, &gs[g]);
     } else {
       int32_t sc = 0;
       while (((int64_t)1 << sc) < ng) ++sc;
-      rc = gg_rmat(rng_u64(&r), sc, (int64_t)rmat_ef * ng, a, b, c, ng, 1, &gs[g]);
+      rc = ipgc_gen_rmat(rng_u64(&r), sc, (int64_t)rmat_ef * ng, a, b, c, ng, 1, &gs[g]);
     }
-    if (rc != GG_OK) {
+    if (rc != IPGC_GEN_OK) {
 #pragma omp critical
       failed = rc;
     }
   }
-  if (failed != GG_OK) {
-    for (int32_t g = 0; g < num_graphs; ++g) gg_free_csr(&gs[g]);
+  if (failed != IPGC_GEN_OK) {
+    for (int32_t g = 0; g < num_graphs; ++g) ipgc_gen_free_csr(&gs[g]);
     free(gs);
     return failed;
   }
@@ -717,9 +726,9 @@ int gg_batch(uint64_t seed, int32_t num_graphs, int32_t nmin, int32_t nmax, doub
   if (!node_off || !edge_off) {
     free(node_off);
     free(edge_off);
-    for (int32_t g = 0; g < num_graphs; ++g) gg_free_csr(&gs[g]);
+    for (int32_t g = 0; g < num_graphs; ++g) ipgc_gen_free_csr(&gs[g]);
     free(gs);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
   node_off[0] = 0;
   edge_off[0] = 0;
@@ -736,16 +745,16 @@ int gg_batch(uint64_t seed, int32_t num_graphs, int32_t nmin, int32_t nmax, doub
     free(cl);
     free(node_off);
     free(edge_off);
-    for (int32_t g = 0; g < num_graphs; ++g) gg_free_csr(&gs[g]);
+    for (int32_t g = 0; g < num_graphs; ++g) ipgc_gen_free_csr(&gs[g]);
     free(gs);
-    return GG_ERR_OOM;
+    return IPGC_GEN_ERR_OOM;
   }
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t g = 0; g < num_graphs; ++g) {
     memcpy(rp + node_off[g] + g, gs[g].rowptr, ((size_t)gs[g].n + 1) * sizeof(int32_t));
     if (gs[g].nnz > 0)
       memcpy(cl + edge_off[g], gs[g].col, (size_t)gs[g].nnz * sizeof(int32_t));
-    gg_free_csr(&gs[g]);
+    ipgc_gen_free_csr(&gs[g]);
   }
   free(gs);
   out->num_graphs = num_graphs;
@@ -753,10 +762,10 @@ int gg_batch(uint64_t seed, int32_t num_graphs, int32_t nmin, int32_t nmax, doub
   out->edge_off = edge_off;
   out->rowptr_cat = rp;
   out->col_cat = cl;
-  return GG_OK;
+  return IPGC_GEN_OK;
 }
 
-void gg_free_batch(gg_batch_t* bt) {
+void ipgc_gen_free_batch(ipgc_gen_batch_t* bt) {
   if (!bt) return;
   free(bt->node_off);
   free(bt->edge_off);
@@ -768,7 +777,7 @@ void gg_free_batch(gg_batch_t* bt) {
 /* ---------------------------------------------------------------- hash -- */
 
 /* FNV-1a (64-bit) over little-endian 32-bit words, used to record inputs. */
-uint64_t gg_hash_words(const int32_t* p, int64_t count, uint64_t h) {
+uint64_t ipgc_gen_hash_words(const int32_t* p, int64_t count, uint64_t h) {
   if (h == 0) h = 0xcbf29ce484222325ULL;
   for (int64_t i = 0; i < count; ++i) {
     uint32_t w = (uint32_t)p[i];
@@ -780,7 +789,7 @@ uint64_t gg_hash_words(const int32_t* p, int64_t count, uint64_t h) {
   return h;
 }
 
-int gg_num_threads(void) {
+int ipgc_gen_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
 #else

@@ -167,3 +167,78 @@ def test_ctx_create_reports_no_device_without_crash(lib):
     rc = lib.ipgc_ctx_create(ctypes.byref(h), 0)
     assert rc in (ipgc.IPGC_ERR_INVALID, ipgc.IPGC_ERR_CUDA)
     assert not h.value
+
+
+# ------------------------------------------------ the generator library --
+
+def declared_generator_symbols():
+    txt = open(os.path.join(ROOT, "include", "ipgc_graphgen.h")).read()
+    return set(re.findall(r"IPGC_GEN_API\s+[\w\s\*]+?\b(ipgc_gen_\w+)\s*\(", txt))
+
+
+def test_generator_library_exports_exactly_its_header():
+    path = graphgen.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True)
+    exported = set(re.findall(r"\bT (\w+)", out.stdout))
+    declared = declared_generator_symbols()
+    assert {"ipgc_gen_er", "ipgc_gen_rmat", "ipgc_gen_road", "ipgc_gen_batch",
+            "ipgc_gen_from_edges", "ipgc_gen_free_csr", "ipgc_gen_free_batch"} <= declared
+    assert exported == declared, (exported ^ declared)
+
+
+def test_generator_c_abi_from_a_c_program(tmp_path):
+    # a C program compiled against include/ipgc_graphgen.h and linked with
+    # libgraphgen.so: the symmetriser on a hand-made edge list (a triangle
+    # 0-1-2 given with a repeat, a reversed copy and a self-loop, plus the
+    # pendant edge 3-1) must give rows {1,2} {0,2,3} {0,1} {1}; an argument
+    # out of range must be refused without memory; the layouts of both
+    # records must match the ctypes mirrors
+    path = graphgen.build()
+    src = tmp_path / "gen.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "ipgc_graphgen.h"
+int main(void) {
+  const int32_t s[] = {0, 1, 2, 1, 2, 3, 2};
+  const int32_t d[] = {1, 2, 0, 0, 2, 1, 1};
+  ipgc_gen_csr g;
+  int rc = ipgc_gen_from_edges(4, 7, s, d, &g);
+  printf("rc %d n %d nnz %lld\n", rc, g.n, (long long)g.nnz);
+  printf("rowptr"); for (int i = 0; i <= g.n; ++i) printf(" %d", g.rowptr[i]); printf("\n");
+  printf("col"); for (long long i = 0; i < g.nnz; ++i) printf(" %d", g.col[i]); printf("\n");
+  ipgc_gen_free_csr(&g);
+  ipgc_gen_free_csr(&g);
+  ipgc_gen_csr bad;
+  const int32_t s2[] = {0}, d2[] = {4};
+  bad.rowptr = (int32_t*)&rc;
+  rc = ipgc_gen_from_edges(4, 1, s2, d2, &bad);
+  printf("bad %d %d\n", rc, bad.rowptr == NULL && bad.col == NULL);
+  printf("er %d\n", ipgc_gen_er(1, 3, 4, &bad));
+  printf("csr %zu %zu %zu %zu %zu\n", sizeof(ipgc_gen_csr), offsetof(ipgc_gen_csr, n),
+         offsetof(ipgc_gen_csr, nnz), offsetof(ipgc_gen_csr, rowptr), offsetof(ipgc_gen_csr, col));
+  printf("batch %zu %zu %zu %zu %zu %zu\n", sizeof(ipgc_gen_batch_t),
+         offsetof(ipgc_gen_batch_t, num_graphs), offsetof(ipgc_gen_batch_t, node_off),
+         offsetof(ipgc_gen_batch_t, edge_off), offsetof(ipgc_gen_batch_t, rowptr_cat),
+         offsetof(ipgc_gen_batch_t, col_cat));
+  return 0;
+}
+''')
+    exe = tmp_path / "gen"
+    libdir = os.path.dirname(path)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src),
+                    "-L", libdir, "-l:libgraphgen.so", f"-Wl,-rpath,{libdir}"], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    assert lines[0] == "rc 0 n 4 nnz 8"
+    assert lines[1] == "rowptr 0 2 5 7 8"
+    assert lines[2] == "col 1 2 0 2 3 0 1 1"
+    assert lines[3] == "bad -1 1"
+    assert lines[4] == "er -1"  # 4 edges do not fit on 3 nodes
+    csr = [int(x) for x in lines[5].split()[1:]]
+    C = graphgen._Csr
+    assert csr == [ctypes.sizeof(C), C.n.offset, C.nnz.offset, C.rowptr.offset, C.col.offset]
+    bat = [int(x) for x in lines[6].split()[1:]]
+    B = graphgen._Batch
+    assert bat == [ctypes.sizeof(B), B.num_graphs.offset, B.node_off.offset, B.edge_off.offset,
+                   B.rowptr_cat.offset, B.col_cat.offset]
