@@ -20,7 +20,7 @@ struct ipgc_ctx {
   size_t ws_bytes = 0;
   Ctrl* d_ctrl = nullptr;
   Ctrl* h_ctrl = nullptr;  // pinned
-  int* d_err = nullptr;
+  ipgc::ValidateState* d_err = nullptr;
   int* h_err = nullptr;  // pinned
   // device copies for ipgc_color_host
   int32_t* d_rowptr = nullptr;
@@ -307,7 +307,7 @@ int check_graph_args(const int32_t* rowptr, const int32_t* col, int32_t n, int64
 
 int run_validate(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
                  cudaStream_t s) {
-  IPGC_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+  IPGC_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(ipgc::ValidateState), s));
   int blocks = ctx->num_sms * 8;
   IPGC_CUDA(ctx, ipgc::launch_validate(rowptr, col, n, nnz, ctx->d_err, blocks, s));
   IPGC_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -424,7 +424,7 @@ int ipgc_ctx_create(ipgc_ctx** out, int device) {
   if (e == cudaSuccess) e = ipgc::occupancy_push(512, &ctx->pocc512);
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_ctrl, sizeof(Ctrl));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_ctrl, sizeof(Ctrl));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(ipgc::ValidateState));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_err, sizeof(int));
   if (e != cudaSuccess) rc = cuda_fail(ctx, e);
   if (rc == IPGC_OK && (!coop || ctx->occ256 < 1 || ctx->occ512 < 1 || ctx->pocc256 < 1 ||

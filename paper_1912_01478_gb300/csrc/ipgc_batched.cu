@@ -462,11 +462,11 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   w += b_pq;
   int32_t* d_pw = (int32_t*)w;
   w += b_pw;
-  int* d_err = (int*)w;
+  ipgc::ValidateState* d_err = (ipgc::ValidateState*)w;
 
   // optional validation of every graph (one launch per graph)
   if (o.base.validate) {
-    BCUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    BCUDA(cudaMemsetAsync(d_err, 0, sizeof(ipgc::ValidateState), s));
     for (int32_t g = 0; g < num_graphs; ++g) {
       const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
       if (n == 0) continue;

@@ -129,46 +129,214 @@ __global__ void finish_kernel(Params p, int last_round) {
 }
 
 // ------------------------------------------------------------- validation --
+//
+// The input check of Section V's preprocessing (no self-loop, no multi-edge)
+// and of the undirected graph of Section II-A (symmetric CSR), in three
+// launches on one stream. The state is ValidateState: `err` collects the
+// failed checks' bits (the caller clears it), `resp` counts the entries whose
+// reverse was searched and is reset by the last launch.
+//
+// 1. validate_rowptr_kernel: rowptr[0] == 0, rowptr[n] == nnz, rowptr
+//    non-decreasing (so every later index is in bounds).
+// 2. validate_entries_kernel, skipped when (1) failed: every entry (v, u) is in
+//    range, not a self-loop and above its left neighbour in the row (rows
+//    strictly ascending: sorted, no duplicates). For symmetry each undirected
+//    pair is searched once, from the end whose (degree, ID) is larger, in the
+//    other end's (no longer) row; those entries are counted in `resp`.
+// 3. validate_count_kernel: with every row free of duplicates and every
+//    searched reverse found, the map (v, u) -> (u, v) sends the counted
+//    entries one to one into the uncounted ones, so the CSR is symmetric iff
+//    also 2 resp == nnz.
+//
+// Entries are dealt to warps edge-balanced along the merge path of the row
+// ends and the entry indices (n + nnz items), so a hub's row is spread over
+// many warps and a run of short or empty rows over few. Each warp takes a
+// contiguous range of tiles of 32 x kValIpt consecutive items; it finds the
+// row its first tile starts in with a 32-way search of rowptr, and every
+// later tile starts where the previous one ended. Per tile the warp stages
+// the row offsets and entries in shared memory with coalesced loads, and each
+// lane decodes its kValIpt consecutive items from there, then loads all
+// their other rows' offsets, then runs their lookups side by side.
 
-// One warp per row: offsets sane, entries in range, no self-loop, strictly
-// ascending, and every (v, u) has its (u, v) (binary search in row u).
-__global__ void validate_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                int32_t n, int64_t nnz, int* err) {
-  const int lane = lane_id();
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  if (gw == 0 && lane == 0) {
-    if (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz) atomicOr(err, 1);
+constexpr int kValIpt = 8;                // merge-path items per lane
+constexpr int kValTile = 32 * kValIpt;    // items per warp tile
+constexpr int kValBlock = 256;
+
+__global__ void validate_rowptr_kernel(const int32_t* __restrict__ rowptr, int32_t n, int64_t nnz,
+                                       ValidateState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int bad = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+    const int32_t a = __ldg(rowptr + v);
+    if (v == 0 && a != 0) bad |= 1;
+    if (v == n && (int64_t)a != nnz) bad |= 1;
+    if (a < 0 || (int64_t)a > nnz) bad |= 2;
+    if (v < n && __ldg(rowptr + v + 1) < a) bad |= 2;
   }
-  for (int64_t v = gw; v < n; v += nw) {
-    const int s = rowptr[v], e = rowptr[v + 1];
-    if (s < 0 || e < s || (int64_t)e > nnz) {
-      if (lane == 0) atomicOr(err, 2);
-      continue;
+  bad = __reduce_or_sync(FULL, bad);
+  if (bad && lane_id() == 0) atomicOr(&st->err, bad);
+}
+
+// Rows consumed on the merge path after the first d items: the row end of
+// row j comes after entry rowptr[j + 1] - 1 and before entry rowptr[j + 1],
+// so it is item j + rowptr[j + 1]; count the j in [0, n) with that item < d
+// (a prefix of the rows). All 32 lanes call it and get the same value.
+__device__ __forceinline__ int64_t merge_rows_before(const int32_t* rowptr, int32_t n, int64_t nnz,
+                                                     int64_t d) {
+  const int lane = lane_id();
+  int64_t lo = d - nnz > 0 ? d - nnz : 0;  // rows [0, lo) are certainly consumed
+  int64_t hi = d < n ? d : n;              // rows [hi, n) certainly not
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t j = lo + lane * step;
+    const bool p = j < hi && (int64_t)__ldg(rowptr + j + 1) + j < d;
+    const int c = __popc(__ballot_sync(FULL, p));  // the true probes are a prefix
+    if (c == 0) {
+      hi = lo;
+    } else {
+      const int64_t nlo = lo + (int64_t)(c - 1) * step + 1;
+      hi = hi < lo + (int64_t)c * step ? hi : lo + (int64_t)c * step;
+      lo = nlo;
     }
-    for (int k = s + lane; k < e; k += 32) {
-      const int u = col[k];
-      if (u < 0 || u >= n || u == (int)v) {
-        atomicOr(err, 4);
-        continue;
-      }
-      if (k > s && col[k - 1] >= u) atomicOr(err, 8);
-      const int lo0 = rowptr[u], hi0 = rowptr[u + 1];
-      if (lo0 < 0 || hi0 < lo0 || (int64_t)hi0 > nnz) {
-        atomicOr(err, 2);
-        continue;
-      }
-      int lo = lo0, hi = hi0;  // search v in col[lo, hi)
+  }
+  const int64_t j = lo + lane;
+  const bool p = j < hi && (int64_t)__ldg(rowptr + j + 1) + j < d;
+  return lo + __popc(__ballot_sync(FULL, p));
+}
+
+__global__ void __launch_bounds__(kValBlock)
+validate_entries_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                        int32_t n, int64_t nnz, ValidateState* st) {
+  constexpr int kWarps = kValBlock / 32;
+  __shared__ int32_t s_row[kWarps][kValTile + 2];  // rowptr[i0 .. i0 + kValTile + 1]
+  __shared__ int32_t s_col[kWarps][kValTile];      // col[k0 .. k0 + kValTile)
+  __shared__ unsigned long long s_resp[kWarps];
+  if (*reinterpret_cast<volatile int*>(&st->err) != 0) return;  // rowptr is not safe to follow
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  int32_t* sr = s_row[warp];
+  int32_t* sc = s_col[warp];
+  const int64_t total = (int64_t)n + nnz;
+  const int64_t ntiles = (total + kValTile - 1) / kValTile;
+  // each warp walks a contiguous range of tiles: one search for its start,
+  // then every tile starts where the previous one ended
+  const int64_t nw = (int64_t)gridDim.x * kWarps, gw = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t t_lo = ntiles * gw / nw, t_hi = ntiles * (gw + 1) / nw;
+  unsigned long long resp = 0;
+  int bad = 0;
+  int64_t i0 = t_lo < t_hi ? merge_rows_before(rowptr, n, nnz, t_lo * kValTile) : 0;
+  for (int64_t tile = t_lo; tile < t_hi; ++tile) {
+    const int64_t d0 = tile * kValTile;
+    const int64_t k0 = d0 - i0;
+    const int nr = (int)min((int64_t)kValTile + 2, (int64_t)n + 1 - i0);
+    const int nc = (int)min((int64_t)kValTile, nnz - k0);
+    __syncwarp();  // the previous tile's readers are done
+    for (int j = lane; j < nr; j += 32) sr[j] = __ldg(rowptr + i0 + j);
+    for (int j = lane; j < nc; j += 32) sc[j] = __ldg(col + k0 + j);
+    __syncwarp();
+    // this lane's items [td, td + kValIpt): its start row from the staged offsets
+    const int64_t td = d0 + (int64_t)lane * kValIpt;
+    int64_t i = i0, k = 0;
+    if (td < total) {
+      int lo = 0, hi = (int)min((int64_t)kValTile, (int64_t)n - i0);
       while (lo < hi) {
-        const int mid = lo + ((hi - lo) >> 1);
-        if (col[mid] < (int)v)
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)sr[mid + 1] + i0 + mid < td)
           lo = mid + 1;
         else
           hi = mid;
       }
-      if (lo >= hi0 || col[lo] != (int)v) atomicOr(err, 16);
+      i = i0 + lo;
+      k = td - i;
     }
+    // pass 1, registers only: the lane's entries (v, u), the layout checks
+    int32_t vq[kValIpt], uq[kValIpt], dq[kValIpt];
+#pragma unroll
+    for (int q = 0; q < kValIpt; ++q) {
+      vq[q] = -1;
+      uq[q] = -1;
+      dq[q] = 0;
+      if (td + q >= total) continue;
+      const int ri = (int)(i - i0);
+      if (i < n && (int64_t)sr[ri + 1] <= k) {  // the end of row i
+        ++i;
+        continue;
+      }
+      const int32_t v = (int32_t)i;
+      const int32_t sv = sr[ri];
+      const int32_t u = sc[k - k0];
+      if (u < 0 || u >= n || u == v) {
+        bad |= 4;
+      } else {
+        if (k > sv && (k - 1 >= k0 ? sc[k - 1 - k0] : __ldg(col + k - 1)) >= u) bad |= 8;
+        vq[q] = v;
+        uq[q] = u;
+        dq[q] = sr[ri + 1] - sv;
+      }
+      ++k;
+    }
+    // the next tile starts where lane 31's items ended
+    i0 = __shfl_sync(FULL, i, 31);
+    // pass 2: every entry's other row (independent loads)
+    int32_t aq[kValIpt], bq[kValIpt];
+#pragma unroll
+    for (int q = 0; q < kValIpt; ++q) {
+      aq[q] = 0;
+      bq[q] = 0;
+      if (uq[q] >= 0) {
+        aq[q] = __ldg(rowptr + uq[q]);
+        bq[q] = __ldg(rowptr + uq[q] + 1);
+      }
+    }
+    // pass 3: the entries that search (larger (degree, ID) end), all their
+    // binary searches advanced together
+    bool act[kValIpt], fnd[kValIpt];
+#pragma unroll
+    for (int q = 0; q < kValIpt; ++q) {
+      const int32_t du = bq[q] - aq[q];
+      act[q] = uq[q] >= 0 && (du < dq[q] || (du == dq[q] && uq[q] < vq[q]));
+      fnd[q] = false;
+      resp += act[q];
+    }
+    bool any = true;
+    while (any) {
+      any = false;
+#pragma unroll
+      for (int q = 0; q < kValIpt; ++q) {
+        if (act[q] && aq[q] < bq[q]) {
+          const int m = aq[q] + ((bq[q] - aq[q]) >> 1);
+          const int32_t x = __ldg(col + m);
+          if (x == vq[q]) {
+            fnd[q] = true;
+            act[q] = false;
+          } else if (x < vq[q]) {
+            aq[q] = m + 1;
+          } else {
+            bq[q] = m;
+          }
+          any |= act[q] && aq[q] < bq[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kValIpt; ++q)
+      if (act[q] && !fnd[q]) bad |= 16;  // searched and not found
   }
+  // one atomic per CTA for the count, one per warp for a failure
+  bad = __reduce_or_sync(FULL, bad);
+  if (bad && lane == 0) atomicOr(&st->err, bad);
+  for (int o = 16; o > 0; o >>= 1) resp += __shfl_down_sync(FULL, resp, o);
+  if (lane == 0) s_resp[warp] = resp;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sum = 0;
+    for (int w = 0; w < kWarps; ++w) sum += s_resp[w];
+    if (sum) atomicAdd(&st->resp, sum);
+  }
+}
+
+__global__ void validate_count_kernel(int64_t nnz, ValidateState* st) {
+  if (st->err == 0 && 2 * (int64_t)st->resp != nnz) st->err |= 32;
+  st->resp = 0;
 }
 
 // ------------------------------------------------------------ host launch --
@@ -257,8 +425,20 @@ cudaError_t launch_finish(const Params& p, int last_round, cudaStream_t s) {
 }
 
 cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
-                            int* d_err, int blocks, cudaStream_t s) {
-  validate_kernel<<<blocks, 256, 0, s>>>(rowptr, col, n, nnz, d_err);
+                            ValidateState* st, int blocks, cudaStream_t s) {
+  if (blocks < 1) blocks = 1;
+  // the row offsets: four per thread and launch at most
+  const int64_t want = ((int64_t)n + 1 + 4 * kValBlock - 1) / (4 * kValBlock);
+  validate_rowptr_kernel<<<(int)(want < blocks ? want : blocks), kValBlock, 0, s>>>(rowptr, n, nnz, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = ((int64_t)n + nnz + kValTile - 1) / kValTile;
+  const int64_t eb = (tiles + kValBlock / 32 - 1) / (kValBlock / 32);
+  validate_entries_kernel<<<(int)(eb < blocks ? eb : blocks), kValBlock, 0, s>>>(rowptr, col, n, nnz,
+                                                                               st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  validate_count_kernel<<<1, 1, 0, s>>>(nnz, st);
   return cudaGetLastError();
 }
 

@@ -37,6 +37,15 @@ constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
 constexpr int kPushMaxC = 32 * kGWords;  // forbidden-colour bitmaps hold colours 1..2048
 constexpr int kPushChunk = 128;  // row entries per queued push item (one warp window)
 
+// State of the CSR check (launch_validate): the failed checks' bits (cleared
+// by the caller) and the count of entries whose reverse was searched (reset by
+// the check's last launch).
+struct ValidateState {
+  int32_t err;
+  int32_t pad;
+  unsigned long long resp;
+};
+
 // Per-colouring control block in device memory. Zeroed before every launch.
 struct Ctrl {
   int32_t cnt[2][4];               // worklist size per parity: [B_SMALL] nodes, [B_BIG] nodes

@@ -35,7 +35,7 @@ cudaError_t launch_assign(const Params& p, int bs, int blocks, int round, int mo
 cudaError_t launch_detect(const Params& p, int bs, int blocks, int round, int mode, cudaStream_t s);
 cudaError_t launch_finish(const Params& p, int last_round, cudaStream_t s);
 cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int32_t n, int64_t nnz,
-                            int* d_err, int blocks, cudaStream_t s);
+                            ValidateState* st, int blocks, cudaStream_t s);
 
 // Batched colouring (ipgc_batched.cu).
 cudaError_t occupancy_batched(int bs, int* blocks_per_sm, bool push = false);
