@@ -233,21 +233,29 @@ IPGC_API int ipgc_color_host(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t
                     const ipgc_options* opt, void* stream);
 
 /*
- * Check a CSR graph: rowptr[0] == 0, rowptr non-decreasing, rowptr[n] == nnz,
- * every col entry in [0, n), no self-loop, rows strictly ascending (sorted,
- * no duplicates) and symmetric (u in row v iff v in row u).
- * on_device = 1: rowptr/col are device pointers and a kernel checks them on
- * the context's stream (ctx may be NULL: current device, default stream);
+ * Check that a CSR is an input the method is defined on: the undirected graph
+ * G = (V, E) of the problem statement (Section II-A), so symmetric (u in row
+ * v iff v in row u), with the self-loops and multi-edges removed (Section V),
+ * so no entry (v, v) and no duplicate entry; also rowptr[0] == 0, rowptr
+ * non-decreasing, rowptr[n] == nnz, every col entry in [0, n) and every row
+ * ascending (the layout the colouring kernels read).
+ * on_device = 1: rowptr/col are device pointers and kernels check them on
+ * the context's stream (ctx may be NULL: current device, default stream;
+ * the call waits for the stream); every entry is read once and each
+ * undirected pair is looked up once, in the shorter of its two rows.
  * on_device = 0: host pointers, checked on the host. Returns IPGC_OK or
- * IPGC_ERR_INVALID.
+ * IPGC_ERR_INVALID (also for n < 0, nnz outside [0, 2^31) or a NULL
+ * pointer), IPGC_ERR_CUDA, IPGC_ERR_OOM.
  */
 IPGC_API int ipgc_validate_csr(ipgc_ctx* ctx, const int32_t* rowptr, const int32_t* col, int32_t n,
                       int64_t nnz, int on_device, void* stream);
 
 /*
- * Batched colouring: many independent graphs in one persistent launch. Each
- * graph gets exactly the colouring ipgc_color_ex would give it alone (own
- * worklists, rounds and mode decisions, Sections II-C and IV). A graph is
+ * Batched colouring: many independent graphs in one persistent launch. The
+ * paper colours one graph per run; this form applies its loop (Section
+ * II-C) and hybrid schedule (Section IV) to every graph of a batch, each
+ * graph with its own worklists, rounds and mode decisions, so each graph gets
+ * exactly the colouring ipgc_color_ex would give it alone. A graph is
  * coloured by a team of k CTAs, k the smallest power of two with
  * k * nnz_per_cta >= its entries, or min(max_team, grid) where that is
  * smaller; teams are gang-scheduled on aligned blocks of CTAs, largest
@@ -307,7 +315,9 @@ IPGC_API int ipgc_batch_plan(int32_t num_graphs, const int32_t* n, const int64_t
                              int32_t* first_cta, int32_t* seq);
 
 /*
- * Colouring server with continuous batching. Requests are host
+ * Colouring server with continuous batching (not in the paper: a serving
+ * form of Section II-C's loop, whose results are those of colouring each
+ * request alone with the batched phases above). Requests are host
  * CSR graphs, copied into pinned staging at submission and queued in order.
  * A scheduler thread admits queued requests while the device arena (one
  * allocation of hbm_budget bytes) has room for the graph, its colours and its
@@ -420,8 +430,10 @@ IPGC_API int ipgc_mlp_train(ipgc_ctx* ctx, const float* x, const float* y, const
 IPGC_API int ipgc_policy_load(ipgc_ctx* ctx, const float* w, int32_t len);
 
 /*
- * Schedule autotuners. The schedule (t1, chunk, block_size and,
- * for batches, max_team and nnz_per_cta) changes speed only, never a
+ * Schedule autotuners. The paper maps work to threads with Nested
+ * Parallelism and tunes nothing per input (Section V); here the mapping's
+ * knobs (t1, chunk, block_size and, for batches, max_team and nnz_per_cta)
+ * are chosen by timing. The schedule changes speed only, never a
  * colour. Starting from *opt, each knob in turn is set to every candidate
  * value, the colouring is timed (best of `reps`, CUDA events on `stream`) and
  * the fastest value is kept; *opt receives the result and *best_ms (may be
@@ -472,20 +484,31 @@ IPGC_API int ipgc_push_bench(ipgc_ctx* ctx, int64_t n, int32_t count, int32_t mo
  * Colour one graph without allocating anything (the paper has no counterpart;
  * this exists for callers that cannot allocate device memory when they need
  * a colouring, e.g. code running inside an allocator or memory-pool callback,
- * or under a budget reserved up front). Same result as ipgc_color_ex with
- * default options; the CSR is always validated.
+ * which must not re-enter the allocator, or a service that works within a
+ * budget reserved up front). The CSR is always validated. The colouring is
+ * the rescanning one (every round rereads the active nodes' rows) with the
+ * default degree bound t1 = 64 fixed and the default work items and
+ * threshold rule; colours, rounds, num_colors, rounds_topo and rounds_data
+ * equal those of ipgc_color_ex with default options (edges_processed and ns
+ * describe this call's own work).
  *   rowptr, col   device pointers as for ipgc_color_ex
  *   n, nnz        at most IPGC_NOALLOC_MAX_N nodes and IPGC_NOALLOC_MAX_NNZ
  *                 entries; larger graphs return IPGC_ERR_TOO_LARGE before any
  *                 CUDA call
  *   colors_out    device pointer, int32[n]
- *   stats_out     host pointer or NULL; non-NULL waits for the stream
+ *   stats_out     host pointer or NULL
  *   stream        cudaStream_t or NULL
- * Working memory is one fixed device array inside the library (about 25 MB,
- * held on every GPU that loads the library until the process exits), shared
- * by all calls: calls that overlap on one GPU race and must be serialised by
- * the caller. No cudaMalloc or cudaFree is made. The first call on a device
- * looks up the array's device address, so make it before any stream capture.
+ * The call waits for `stream` (after validation and after the colouring) and
+ * returns the error the device reported, with or without stats_out.
+ * Working memory is one fixed device array inside the library (15,074,048
+ * bytes), shared by all calls: calls that overlap on one GPU race and must be
+ * serialised by the caller. No cudaMalloc or cudaFree is made. The first call
+ * on a device looks up the array's device address, which also loads the
+ * library's device code, and the array with it, onto that device if nothing
+ * else did (lazy module loading); so make that first call at set-up (an
+ * empty graph, n = 0, will do), before any stream capture and before the
+ * point where allocating is no longer possible. The device then holds the
+ * array until the process exits.
  * Errors: IPGC_ERR_INVALID, IPGC_ERR_TOO_LARGE, IPGC_ERR_TIMEOUT,
  * IPGC_ERR_NO_CONVERGE, IPGC_ERR_CUDA, IPGC_ERR_UNSUPPORTED.
  */

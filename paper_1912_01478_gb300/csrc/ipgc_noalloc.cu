@@ -8,13 +8,25 @@
 // takes its working memory from one file-scope device array of fixed size
 // instead of cudaMalloc. Inputs and outputs are still the caller's.
 //
-// The array below is part of the loaded library's device image: every GPU on
-// which the library's kernels are loaded holds it (kScratchBytes, about 25 MB)
-// until the process exits. Every call on a device shares that device's copy,
-// which keeps the contents of the last call; calls that overlap on one GPU
-// (from different streams or host threads) overwrite each other's state, so
-// the caller must serialise them. What must start at zero (the control block
-// and the validation flag) is cleared by every call.
+// The array below belongs to the library's device code (kScratchBytes =
+// 15,074,048 bytes, about 15.1 MB). With lazy module loading (the CUDA
+// default) that code, and with it the array, is loaded onto a GPU the first
+// time the process uses it there; the first call of this entry point on a
+// device looks up the array's address, which loads it if nothing else did.
+// That call should therefore be made at set-up, before any stream capture and
+// before the moment when allocating is no longer possible; an empty graph
+// (n = 0) will do. From then on the device holds the array until the process
+// exits. Every call on a device shares that device's copy, which keeps the
+// contents of the last call; calls that overlap on one GPU (from different
+// streams or host threads) overwrite each other's state, so the caller must
+// serialise them. What must start at zero (the control block and the
+// validation state) is cleared by every call.
+//
+// The colouring is the rescanning one of ipgc_color_ex (every round rereads
+// the active nodes' rows) with the default degree bound t1 = 64 fixed, the
+// default work-item size and threshold rule, without forbidden-colour bitmaps
+// or neighbour filtering; its colours, rounds and mode counts are those of
+// ipgc_color_ex with default options.
 #include <cstring>
 #include <mutex>
 
@@ -100,19 +112,21 @@ extern "C" IPGC_API int ipgc_color_noalloc(const int32_t* rowptr, const int32_t*
   if (n > 0 && (!rowptr || !colors_out)) return IPGC_ERR_INVALID;
   if (nnz > 0 && (!col || n == 0)) return IPGC_ERR_INVALID;
   if (stats_out) std::memset(stats_out, 0, sizeof(*stats_out));
-  if (n == 0) return IPGC_OK;
 
+  // the per-device set-up comes first, so that an empty call made at
+  // initialisation already reserves the array
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return IPGC_ERR_CUDA;
   DeviceSetup ds;
   int rc = setup_device(dev, &ds);
   if (rc != IPGC_OK) return rc;
+  if (n == 0) return IPGC_OK;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* base = ds.scratch;
 
-  // the control block and the validation flag must start at zero
+  // the control block and the validation state must start at zero
   if (cudaMemsetAsync(base, 0, (size_t)kOffTent, s) != cudaSuccess) return IPGC_ERR_CUDA;
-  int* d_err = reinterpret_cast<int*>(base + kOffErr);
+  ValidateState* d_err = reinterpret_cast<ValidateState*>(base + kOffErr);
   if (launch_validate(rowptr, col, n, nnz, d_err, ds.sms * 8, s) != cudaSuccess) return IPGC_ERR_CUDA;
   int h_err = 0;
   if (cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -146,18 +160,21 @@ extern "C" IPGC_API int ipgc_color_noalloc(const int32_t* rowptr, const int32_t*
   p.timeout_ns = 10000000000ull;
   p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
   if (launch_persistent(p, 256, ds.occ * ds.sms, 0, s) != cudaSuccess) return IPGC_ERR_CUDA;
-  if (!stats_out) return IPGC_OK;
 
+  // the call always waits for the colouring, so that an error the device
+  // reported (a bounded wait that expired, too many rounds) is returned
   Ctrl h;
   if (cudaMemcpyAsync(&h, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return IPGC_ERR_CUDA;
-  stats_out->rounds = h.rounds;
-  stats_out->num_colors = h.maxc;
-  stats_out->rounds_topo = h.rounds_topo;
-  stats_out->rounds_data = h.rounds_data;
-  stats_out->edges_processed = (int64_t)h.edges;
-  stats_out->ns = h.t_end >= h.t_start ? h.t_end - h.t_start : 0;
-  stats_out->error = h.status;
+  if (stats_out) {
+    stats_out->rounds = h.rounds;
+    stats_out->num_colors = h.maxc;
+    stats_out->rounds_topo = h.rounds_topo;
+    stats_out->rounds_data = h.rounds_data;
+    stats_out->edges_processed = (int64_t)h.edges;
+    stats_out->ns = h.t_end >= h.t_start ? h.t_end - h.t_start : 0;
+    stats_out->error = h.status;
+  }
   return h.status;
 }
