@@ -161,8 +161,10 @@ typedef struct ipgc_options {
                              (IPGC_ERR_UNSUPPORTED otherwise); turns neighbour filtering off;
                              rounds that start with a colour above 2046 committed rescan; a
                              graph without a node of degree > t1 is coloured by rescanning.
-                             IPGC_FORBIDDEN_AUTO (0, default): PUSH with the persistent driver,
-                             RESCAN with the host-loop driver. */
+                             IPGC_FORBIDDEN_AUTO (0, default): PUSH with the persistent driver
+                             when the rows of the nodes of degree > t1 hold at least half of
+                             the entries (checked on the device before round 1), else RESCAN
+                             (without neighbour filtering); RESCAN with the host-loop driver. */
 } ipgc_options;
 
 #define IPGC_WORKLIST_KEEP 0
@@ -329,8 +331,9 @@ IPGC_API int ipgc_batch_plan(int32_t num_graphs, const int32_t* n, const int64_t
  * the result into pinned staging and raises a host-visible flag), not when
  * its batch ends, and its device memory then admits the next requests at
  * once. Each result is the colouring the graph gets alone (the batched
- * phases). The learned mode
- * policy is not used by the server (IPGC_MODE_LEARNED runs the threshold rule).
+ * phases). With batch.base.mode = IPGC_MODE_LEARNED the network loaded by
+ * ipgc_server_policy_load chooses each round's mode (the threshold rule
+ * without one, or where it is unsure).
  */
 typedef struct ipgc_server ipgc_server;
 
@@ -386,6 +389,15 @@ IPGC_API int ipgc_server_poll(ipgc_server* srv, uint64_t ticket, int32_t* h_colo
 /* The next completed ticket (each reported once); IPGC_PENDING after timeout_ns. */
 IPGC_API int ipgc_server_next_done(ipgc_server* srv, uint64_t* ticket, uint64_t timeout_ns);
 IPGC_API int ipgc_server_query(ipgc_server* srv, ipgc_server_counters* counters);
+/*
+ * The learned mode switch of the server's launches (see ipgc_policy_load):
+ * len = IPGC_MLP_PARAMS host floats, copied into device memory of the
+ * server's own; launches that start afterwards use them (those already
+ * running keep the network they started with). len = 0 unloads. Used only
+ * when the server's batch.base.mode is IPGC_MODE_LEARNED; colours never
+ * depend on it. IPGC_ERR_INVALID (wrong length), IPGC_ERR_OOM, IPGC_ERR_CUDA.
+ */
+IPGC_API int ipgc_server_policy_load(ipgc_server* srv, const float* w, int32_t len);
 /* Finishes admitted work, drops queued requests, frees everything. */
 IPGC_API int ipgc_server_destroy(ipgc_server* srv);
 

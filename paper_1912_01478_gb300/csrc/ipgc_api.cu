@@ -282,6 +282,7 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
   p.col_vec = ((uintptr_t)col & 15u) == 0 ? 1 : 0;
   p.shrink = o.driver == IPGC_DRIVER_PERSISTENT ? 1 : 0;
   p.t1_auto = o.t1 <= 0 ? 1 : 0;  // default t1: chosen on the device
+  p.push_auto = o.forbidden == IPGC_FORBIDDEN_AUTO ? 1 : 0;
   p.wl_rebuild = o.worklist == IPGC_WORKLIST_REBUILD ? 1 : 0;
 }
 

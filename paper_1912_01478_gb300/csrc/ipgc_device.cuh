@@ -69,6 +69,7 @@ struct Ctrl {
   int32_t rbcnt[2];                // worklist rebuild: low-degree nodes, work items
   int32_t t1;                      // the low-degree bound in use (set before round 1)
   int32_t maxdeg;                  // largest degree (when t1 is chosen from it)
+  unsigned long long bigsum;       // entries in the rows of degree > t1 (pushing kernel)
   int32_t pqcnt;                   // push items queued by the current conflict step
   int32_t pwcnt;                   // winners of the current conflict step still to push
   int32_t push_off;                // the pushing kernel found no node of degree > t1 and left
@@ -132,6 +133,8 @@ struct Params {
   int32_t shrink;     // the team may drop CTAs in small data-driven rounds (single graph)
   int32_t wl_rebuild; // topology-driven rounds keep no worklist; it is rebuilt on the way back
   int32_t t1_auto;    // choose t1 on the device: the largest degree if <= kMaxT1, else t1
+  int32_t push_auto;  // pushing kernel: colour with bitmaps only when the rows of degree > t1
+                      // hold at least half of the entries (else leave it to rescanning)
   int64_t handoff_wl; // hand over when |WL| <= handoff_wl (0: never)
   // Forbidden-colour bitmaps (pbits == nullptr: off). A node v of degree
   // d > t1 keeps the colours of its finalised neighbours as a bitmap of
@@ -273,53 +276,96 @@ struct Team {
   int ncta;
 };
 
+// Device-scope atomics and loads with the ordering a barrier needs (PTX
+// memory model): an arrival releases the CTA's writes (ordered before it by
+// __syncthreads) and acquires those of the CTAs that arrived before it; a
+// waiter acquires them all through the generation word.
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* a, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* a) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* a) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+// The top bit of the barrier's generation word: an error has been recorded,
+// so every CTA leaves its barrier (the count lives in the low 31 bits).
+constexpr uint32_t kBarErr = 0x80000000u;
+
+// Records an error of the colouring (the first one wins) and raises the
+// barrier's error bit, so that CTAs waiting in a barrier leave it at once.
+__device__ __forceinline__ void record_error(Ctrl* c, int code) {
+  atomicCAS(&c->status, 0, code);
+  atomicOr(&c->bar_gen, kBarErr);
+}
+
 // Barrier of a team of co-resident CTAs (a cooperative launch guarantees
 // residency), bounded by timeout_ns: a CTA that waits longer records
 // IPGC_ERR_TIMEOUT and leaves the barrier. Returns false when the team must
-// stop (timeout here or an error recorded elsewhere). The counters live in
-// the graph's control block. A team of more than kBarFlat CTAs arrives in
-// kBarGroups groups (atomics on one counter serialise, so 16 short chains
-// and one of 16 beat one of hundreds). `extra` phantom CTAs never arrive
-// (tests).
+// stop (timeout here or an error recorded elsewhere, seen as the error bit of
+// the generation word). The counters live in the graph's control block. A
+// team of more than kBarFlat CTAs arrives in kBarGroups groups (atomics on
+// one counter serialise, so 16 short chains and one of 16 beat one of
+// hundreds). `extra` phantom CTAs never arrive (tests).
+//
+// Thread 0 reads the generation before the CTA's warps meet (the barrier
+// cannot complete before this CTA arrives, and this thread has seen the
+// previous one complete, so the value is the current generation); arrivals
+// are acquire-release atomics and the last arrival releases the next
+// generation with an atomic add, which waiters acquire: no separate fences
+// and no further read after the wait.
 __device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_t timeout_ns,
                                              uint32_t extra = 0) {
   __shared__ int s_ok;
+  uint32_t gen = 0;
+  if (threadIdx.x == 0) gen = ld_relaxed_u32(&c->bar_gen);
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile uint32_t* genp = &c->bar_gen;
-    const uint32_t gen = *genp;
-    __threadfence();
-    bool last;
-    if (ncta > kBarFlat) {
-      // CTAs arrive on kBarGroups counters (CTA i in group i % kBarGroups);
-      // the last of a group resets its counter and arrives on the top one
-      const int g = cta % kBarGroups;
-      const uint32_t gsz = (uint32_t)(ncta / kBarGroups + (g < ncta % kBarGroups ? 1 : 0));
-      last = false;
-      if (atomicAdd(&c->bar_grp[g][0], 1u) == gsz - 1) {
-        c->bar_grp[g][0] = 0;
-        __threadfence();
-        last = atomicAdd(&c->bar_count, 1u) == (uint32_t)kBarGroups + extra - 1;
-      }
-    } else {
-      last = atomicAdd(&c->bar_count, 1u) == (uint32_t)ncta + extra - 1;
-    }
-    if (last) {
-      c->bar_count = 0;
-      __threadfence();
-      atomicAdd(&c->bar_gen, 1u);
-    } else {
-      const uint64_t t0 = gtime();
-      while (*genp == gen) {
-        if (gtime() - t0 > timeout_ns) {
-          atomicCAS(&c->status, 0, IPGC_ERR_TIMEOUT);
-          break;
+    bool ok = (gen & kBarErr) == 0;
+    if (ok) {
+      bool last;
+      if (ncta > kBarFlat) {
+        // CTAs arrive on kBarGroups counters (CTA i in group i % kBarGroups);
+        // the last of a group resets its counter and arrives on the top one
+        const int g = cta % kBarGroups;
+        const uint32_t gsz = (uint32_t)(ncta / kBarGroups + (g < ncta % kBarGroups ? 1 : 0));
+        last = false;
+        if (atom_add_acq_rel(&c->bar_grp[g][0], 1u) == gsz - 1) {
+          c->bar_grp[g][0] = 0;  // ordered before the arrival below
+          last = atom_add_acq_rel(&c->bar_count, 1u) == (uint32_t)kBarGroups + extra - 1;
         }
-        __nanosleep(64);
+      } else {
+        last = atom_add_acq_rel(&c->bar_count, 1u) == (uint32_t)ncta + extra - 1;
+      }
+      if (last) {
+        c->bar_count = 0;  // ordered before the release below
+        ok = (atom_add_acq_rel(&c->bar_gen, 1u) & kBarErr) == 0;
+      } else {
+        const uint64_t t0 = gtime();
+        while (true) {
+          const uint32_t now = ld_acquire_u32(&c->bar_gen);
+          if (now != gen) {
+            ok = (now & kBarErr) == 0;
+            break;
+          }
+          if (gtime() - t0 > timeout_ns) {
+            record_error(c, IPGC_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+          __nanosleep(64);
+        }
       }
     }
-    __threadfence();
-    s_ok = (*(volatile int32_t*)&c->status) == 0;
+    s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;

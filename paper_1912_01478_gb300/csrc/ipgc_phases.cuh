@@ -554,7 +554,7 @@ __device__ inline int item_assign_windowed(const Params& p, unsigned* wb, int s,
   for (int wbase = 0;; wbase += 32 * kGWords) {
     const int wcols = min(lim - wbase, 32 * kGWords);
     if (wcols <= 0) {  // unreachable for a valid graph: some colour <= lim is free
-      if (lane == 0) atomicCAS(&p.ctrl->status, 0, IPGC_ERR_INVALID);
+      if (lane == 0) record_error(p.ctrl, IPGC_ERR_INVALID);
       return lim;
     }
     const int nw = (wcols + 31) >> 5;
@@ -1414,11 +1414,15 @@ __device__ __forceinline__ int decide_mode(const Params& p, int64_t total) {
 // Mode of the round for every thread of the CTA. With IPGC_MODE_LEARNED and
 // a loaded network, warp 0 evaluates it (every CTA of the team computes the
 // same value from the same inputs); the threshold rule decides when the
-// network is unsure (|p - 0.5| < margin) or absent.
+// network is unsure (|p - 0.5| < margin) or absent. A round after a late
+// round (see run_rounds) collects its list nodes' lower-ID winners from the
+// lists, which only the data-driven round does: the learned switch is not
+// asked then (the threshold and data rules give data-driven there anyway).
 template <int BS>
 __device__ __forceinline__ int decide_mode_block(const Params& p, const RoundView& rv,
                                                  int64_t total, Smem<BS>& sm) {
   if (p.policy != IPGC_MODE_LEARNED || !p.mlp) return decide_mode(p, total);
+  if (rv.pull) return MODE_DATA;
   if (threadIdx.x < 32) {
     float f[kMlpIn];
     policy_features(p.n, p.nnz, rv.round, total, rv.nsmall, (int64_t)rv.dsum, rv.maxc, f);
@@ -1863,10 +1867,12 @@ __device__ __forceinline__ int auto_t1(const Params& p, int maxdeg) {
 // The largest degree of the graph into ctrl->maxdeg and, with pushing, the
 // forbidden-colour bitmaps of every node that may keep one (degree > the
 // given t1, which the t1 in use never undercuts where such nodes exist)
-// cleared; then a team barrier.
+// cleared and the entries of their rows counted into ctrl->bigsum; then a
+// team barrier.
 template <int BS>
 __device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm, bool zero) {
   int m = 0;
+  unsigned long long big = 0;
   // four nodes per thread and step: one int4 of row offsets (16-byte aligned
   // rowptr) and the next offset, so a pass over a large graph keeps many
   // loads in flight
@@ -1891,12 +1897,18 @@ __device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm, bool zer
       if (v0 + j >= n) break;
       const int s = r[j], d = r[j + 1] - s;
       m = max(m, d);
-      if (zero && d > p.t1)
+      if (zero && d > p.t1) {
+        big += (unsigned long long)d;
         for (int i = 0, nw = push_words(d); i < nw; ++i) p.pbits[s + i] = 0u;
+      }
     }
   }
   m = block_max<BS>(sm, m);
   if (threadIdx.x == 0 && m > 0) atomicMax(&p.ctrl->maxdeg, m);
+  if (zero) {
+    big = block_sum64<BS>(sm, big);
+    if (threadIdx.x == 0 && big) atomicAdd(&p.ctrl->bigsum, big);
+  }
   return team_barrier(p.ctrl, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
 }
 
@@ -1913,7 +1925,7 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
     const int64_t total = (int64_t)rv.nsmall + rv.nbig;
     if (total == 0) break;
     if (r > p.max_rounds) {
-      if (lead) atomicCAS(&c->status, 0, IPGC_ERR_NO_CONVERGE);
+      if (lead) record_error(c, IPGC_ERR_NO_CONVERGE);
       break;
     }
     if (!FILT && !PUSH && handoff_now(p, r, total, rv.dsum, rv.maxc)) {
@@ -1922,14 +1934,15 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
     }
     rv.mode = decide_mode_block<BS>(p, rv, total, sm);
     // pushing runs a round late when every active node keeps a list of one
-    // work item (rounds after 2, data-driven under the threshold or data
-    // rule, which never go back to topology-driven once |WL| is small): the
-    // active edges are then all on the lists, a winner pushes along its own
-    // list (its active lower-ID neighbours) and the next round's list nodes
-    // collect their lower-ID winners from theirs, so no push phase is needed
+    // work item (rounds after 2, data-driven; the round after a late one is
+    // data-driven too: the threshold and data rules never go back to
+    // topology-driven once |WL| is small, and the learned rule is overruled
+    // there): the active edges are then all on the lists, a winner pushes
+    // along its own list (its active lower-ID neighbours) and the next
+    // round's list nodes collect their lower-ID winners from theirs, so no
+    // push phase is needed
     rv.late = PUSH && rv.push && r >= 3 && rv.mode == MODE_DATA && rv.nsmall == 0 &&
-              rv.odd == 0 && (p.policy == IPGC_MODE_THRESHOLD || p.policy == IPGC_MODE_DATA) &&
-              !p.wl_rebuild;
+              rv.odd == 0 && p.policy != IPGC_MODE_TOPO && !p.wl_rebuild;
     if (p.wl_rebuild && rv.mode == MODE_DATA &&
         (r == 2 || ld_cg(&c->mode_at[(r - 1) & 1]) == MODE_TOPO)) {
       rebuild_worklists<BS>(p, sm, rv, tm);
@@ -2005,6 +2018,12 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
     const int md = ld_cg(&c->maxdeg);
     if (p.t1_auto) t1 = auto_t1(p, md);
     pushing = PUSH && p.pbits != nullptr && md > t1;  // some node keeps a bitmap
+    // chosen automatically, bitmaps are used only when the rows they stand
+    // for hold at least half of the entries: otherwise the pushes of every
+    // committed row cost more than the rescans of the few long rows they
+    // save (a graph with a few giant hubs and few rounds)
+    if (pushing && p.push_auto)
+      pushing = 2 * __ldcg(&c->bigsum) >= (unsigned long long)p.nnz;
   }
   if (PUSH && !pushing) {  // every node on the low-degree path: nothing to push
     if (lead) c->push_off = 1;

@@ -187,6 +187,11 @@ struct ipgc_server {
   bool stop = false;
   int fatal = IPGC_OK;
   std::thread worker;
+  // learned mode switch: the current network (nullptr: none); every network
+  // loaded stays allocated until the server is destroyed, since launches in
+  // flight may still read an earlier one
+  const float* d_mlp = nullptr;
+  std::vector<float*> mlp_bufs;
   // counters
   uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, graphs_in_batches = 0;
   int32_t max_batch_seen = 0;
@@ -339,8 +344,10 @@ bool launch_locked(ipgc_server* S) {
     p.chunk = S->chunk;
     const double h = (double)S->opt.batch.base.threshold_frac * (double)r.n;
     p.H = (int64_t)(h > 0 ? h : 0);
-    p.policy = S->opt.batch.base.mode == IPGC_MODE_LEARNED ? IPGC_MODE_THRESHOLD
-                                                           : S->opt.batch.base.mode;
+    p.policy = S->opt.batch.base.mode;
+    // the network loaded by ipgc_server_policy_load (none: the threshold rule)
+    p.mlp = p.policy == IPGC_MODE_LEARNED ? S->d_mlp : nullptr;
+    p.mlp_margin = S->opt.batch.base.policy_margin;
     p.max_rounds = r.n + 1;
     p.timeout_ns = S->opt.batch.base.timeout_ns ? S->opt.batch.base.timeout_ns : 10000000000ull;
     p.col_vec = 1;  // arena blocks are 256-byte aligned
@@ -408,6 +415,8 @@ void destroy_resources(ipgc_server* S) {
   }
   if (S->d_arena) cudaFree(S->d_arena);
   if (S->h_arena) cudaFreeHost(S->h_arena);
+  for (float* b : S->mlp_bufs) cudaFree(b);
+  S->mlp_bufs.clear();
 }
 
 }  // namespace
@@ -631,6 +640,35 @@ int ipgc_server_query(ipgc_server* S, ipgc_server_counters* c) {
   c->hbm_peak = (int64_t)S->dev.peak();
   c->host_used = (int64_t)S->host.used();
   c->status = S->fatal;
+  return IPGC_OK;
+}
+
+int ipgc_server_policy_load(ipgc_server* S, const float* w, int32_t len) {
+  if (!S || len < 0 || (len > 0 && (!w || len != ipgc::kMlpParams))) return IPGC_ERR_INVALID;
+  if (len == 0) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->d_mlp = nullptr;
+    return IPGC_OK;
+  }
+  // a buffer of its own (launches in flight keep reading the previous one),
+  // filled before it is handed to the scheduler
+  float* buf = nullptr;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(S->device) != cudaSuccess) return IPGC_ERR_CUDA;
+  int rc = IPGC_OK;
+  if (cudaMalloc((void**)&buf, sizeof(float) * (size_t)len) != cudaSuccess)
+    rc = IPGC_ERR_OOM;
+  else if (cudaMemcpy(buf, w, sizeof(float) * (size_t)len, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = IPGC_ERR_CUDA;
+  cudaSetDevice(prev);
+  if (rc != IPGC_OK) {
+    if (buf) cudaFree(buf);
+    return rc;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->mlp_bufs.push_back(buf);
+  S->d_mlp = buf;
   return IPGC_OK;
 }
 

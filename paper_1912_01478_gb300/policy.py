@@ -161,10 +161,12 @@ def _round_times(tr):
 
 
 def collect(ctx: "ipgc.Context", graphs, reps: int = 3, threshold_frac: float = 0.6,
-            forbidden: str = "rescan") -> Traces:
+            forbidden: str = "auto") -> Traces:
     """Forced-mode traces of every (rowptr, col) graph: the median of `reps`
-    runs per mode and round, by default of the paper's loop (rows rescanned
-    every round, which the byte model BYTES_KAPPA describes)."""
+    runs per mode and round, by default of the library's default colouring
+    (forbidden = "auto": bitmaps filled by pushes where a node is above t1);
+    forbidden = "rescan" gives the paper's loop (rows rescanned every round,
+    which the byte model BYTES_KAPPA describes)."""
     import torch
 
     xs, tt, td, thr, gi, ns, ws = [], [], [], [], [], [], []

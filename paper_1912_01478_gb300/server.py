@@ -53,6 +53,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int64)]),
     "ipgc_server_next_done": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64]),
     "ipgc_server_query": (ctypes.c_int, [_P, ctypes.POINTER(ServerCounters)]),
+    "ipgc_server_policy_load": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "ipgc_server_destroy": (ctypes.c_int, [_P]),
 }
 _bound = False
@@ -145,6 +146,17 @@ class Server:
         t = ctypes.c_uint64(0)
         rc = lib().ipgc_server_next_done(self.handle, ctypes.byref(t), int(timeout_s * 1e9))
         return t.value if rc == ipgc.IPGC_OK else None
+
+    def load_policy(self, w):
+        """Load (or with None unload) the network of the learned mode switch."""
+        if w is None:
+            rc = lib().ipgc_server_policy_load(self.handle, None, 0)
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            rc = lib().ipgc_server_policy_load(
+                self.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size)
+        if rc != ipgc.IPGC_OK:
+            raise ipgc.IpgcError(rc, "ipgc_server_policy_load")
 
     def counters(self) -> ServerCounters:
         c = ServerCounters()

@@ -199,3 +199,33 @@ def test_repeated_full_size_colourings_match(ctx):
         colors, st = ctx.color(drp, dcl, options=o)
         got = colors.cpu().numpy()
         assert hashlib.sha256(got.astype("<i4").tobytes()).hexdigest() == exp["colors_sha256"]
+
+
+def test_automatic_choice_between_pushing_and_rescanning(ctx):
+    # by default (IPGC_FORBIDDEN_AUTO) the bitmaps are used only when the rows
+    # of the nodes above t1 hold at least half of the entries: on a graph of a
+    # few giant hubs over a sparse base (the circuit5M stand-in, 29 % of its
+    # entries in rows of degree > 64) no round pushes; on RMAT (most entries
+    # in long rows) the rounds push; the colours are the oracle's either way
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc
+
+    for rp, cl, pushes in ((*graphgen.suite_graph("circuit5M", 0.05), False),
+                           (*graphgen.rmat(15, 16, seed=23), True)):
+        deg = np.diff(rp)
+        share = deg[deg > 64].sum() / cl.size
+        assert (share >= 0.5) == pushes
+        ref = oracle.color(rp, cl, trace=False)
+        drp, dcl = to_dev(rp, cl)
+        tr = ipgc.trace_buffer(rp.size + 1)
+        colors, st = ctx.color(drp, dcl, options=ipgc.ColorOptions(validate=False), trace=tr)
+        assert np.array_equal(colors.cpu().numpy(), ref.colors) and st.rounds == ref.rounds
+        rec = ipgc.read_trace(tr, st.rounds)
+        assert (int(rec["push_ns"].sum()) > 0) == pushes
+        # forced pushing still pushes
+        tr2 = ipgc.trace_buffer(rp.size + 1)
+        colors2, st2 = ctx.color(drp, dcl, options=ipgc.ColorOptions(validate=False, **PUSH),
+                                 trace=tr2)
+        assert np.array_equal(colors2.cpu().numpy(), ref.colors)
+        assert int(ipgc.read_trace(tr2, st2.rounds)["push_ns"].sum()) > 0

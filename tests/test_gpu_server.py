@@ -178,3 +178,41 @@ def test_small_requests_finish_before_a_large_one_in_the_same_launch():
     srv.close()
     assert c.batches == 2 and c.max_batch == len(ts) + 1
     assert order[0] == t0 and order[-1] == tb
+
+
+def test_learned_switch_in_the_server(graphs):
+    # with the learned mode switch the server's launches ask the loaded
+    # network every round: one that always answers "topology-driven" makes
+    # every round of every request topology-driven, one that always answers
+    # "data-driven" every round after the first; without a network the
+    # threshold rule decides; the colours are the oracle's throughout
+    from paper_1912_01478_gb300 import ipgc, server
+
+    gs, refs = graphs
+    o = server.options(inflight=2, max_batch_graphs=8)
+    o.batch.base.mode = ipgc.MODE_LEARNED
+    srv = server.Server(0, o)
+    with pytest.raises(ipgc.IpgcError) as ei:
+        srv.load_policy(np.zeros(10, np.float32))
+    assert ei.value.code == ipgc.IPGC_ERR_INVALID
+    topo = np.zeros(433, np.float32)
+    topo[432] = 10.0  # output bias: p(topology faster) ~ 1
+    data = np.zeros(433, np.float32)
+    data[432] = -10.0
+    wl = [oracle.color(rp, cl).wl_sizes for rp, cl in gs[:12]]
+    for w, want in ((None, "threshold"), (topo, "topo"), (data, "data")):
+        srv.load_policy(w)
+        tickets = [srv.submit(rp, cl) for rp, cl in gs[:12]]
+        for t, ref, (rp, cl), sizes in zip(tickets, refs[:12], gs[:12], wl):
+            while (r := srv.poll(t)) is None:
+                time.sleep(0.0005)
+            check(r, ref)
+            st = r[1]
+            if want == "topo":
+                assert st.rounds_topo == st.rounds
+            elif want == "data":
+                assert st.rounds_topo == min(st.rounds, 1)
+            else:
+                H = int(np.float64(np.float32(0.6)) * (rp.size - 1))  # the library's floor(0.6f n)
+                assert st.rounds_topo == sum(int(x > H) for x in sizes)
+    srv.close()
