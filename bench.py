@@ -15,10 +15,23 @@ Also reported:
                 measured HBM copy peak; per-kernel bytes and device times from
                 the round trace; DRAM traffic from the committed ncu summary
                 when it was taken on the current kernel sources;
+  roofline_dram the DRAM bytes the kernels really move per colouring (ncu
+                summary in profiles/, when taken on the current sources) over
+                the same duration;
+  roofline_own  the bytes the pushing kernel's own steps must move (rows read
+                once at commit, bitmap words, list entries, push atomics, the
+                low-degree nodes' rescans; pushing_bytes) over the duration;
   e2e           the same metric through ipgc_color_host (host buffers, the
                 copies inside the timed region);
-  cpu_baseline  the CPU oracle, single-threaded, on a bounded sample;
-  clocks        nvidia-smi samples taken during the timed region.
+  cpu_baseline  the CPU oracle, single-threaded, on the headline graph itself
+                (host core count and CPU model recorded);
+  clocks        nvidia-smi samples taken during the timed region;
+  validate_ms   the device CSR check of the headline graph, and default_ms a
+                default ipgc_color_ex call (check included);
+  road          the road-network workload (4096^2 grid, seed 3): edges/s and
+                its roofline;
+  batched, serving, mode_rules: compact summaries of those legs (the full
+                records go to --detail FILE).
 
 --impl reference times the CPU oracle on the same metric (host cores).
 With torchrun (N > 1 processes) every rank colours its own replica on its
@@ -66,6 +79,8 @@ def parse():
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000",
                     help="request rates of the serving leg (empty = skip)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--plain-seconds", type=float, default=3.0,
+                    help="wall-time cap of the plain comparator on each rate's stream")
     ap.add_argument("--suite", type=int, default=0,
                     help="Table III analogue on the ten stand-in graphs (slow; 1 = run)")
     ap.add_argument("--mode-rules", type=int, default=1,
@@ -74,6 +89,9 @@ def parse():
                     help="compare the kept and the rebuilt worklist (0 = skip)")
     ap.add_argument("--micro-n", type=int, default=50_912_018,
                     help="nodes of the Section III micro-benchmark leg (0 = skip)")
+    ap.add_argument("--road", type=int, default=1, help="the road-network workload leg (0 = skip)")
+    ap.add_argument("--detail", default="",
+                    help="write the full records of every leg to this JSON file")
     return ap.parse_args()
 
 
@@ -145,16 +163,20 @@ def serving_leg(args, ctx, dev, stream):
         c = srv.counters()
         srv.close()
         lat_ms = np.array(lat, dtype=np.float64) / 1e6
-        # plain path on the first requests of the same stream
-        M = min(N, 200)
+        # the plain path (one ipgc_color_host call per request) on the same
+        # stream, for at most --plain-seconds of wall time (it saturates
+        # near 1 K req/s, so at high rates it serves a prefix of the stream)
         plain_lat = []
         tp0 = time.perf_counter()
-        for i in range(M):
+        for i in range(N):
+            if time.perf_counter() - tp0 > args.plain_seconds:
+                break
             while time.perf_counter() - tp0 < arrivals[i]:
                 pass
             _, _, rp, cl = pinned[pick[i]]
             ctx.color_host(rp, cl, options=None, stream=stream)
             plain_lat.append(time.perf_counter() - tp0 - arrivals[i])
+        M = len(plain_lat)
         plain_wall = time.perf_counter() - tp0
         pl = np.array(plain_lat) * 1e3
         out_rates.append({
@@ -284,24 +306,41 @@ def suite_leg(args, ctx, stream):
             "geomean_push_over_plain": geo("push_over_plain")}
 
 
+def training_graphs():
+    """The learned switch's training graphs: RMAT, road grids, Erdos-Renyi,
+    and 2-D and 3-D random geometric graphs and a lattice (mesh-like), none of
+    them a held-out graph."""
+    from paper_1912_01478_gb300 import graphgen
+
+    gs = [graphgen.rmat(a, b, seed=sd) for a, b, sd in [(15, 16, 1), (16, 8, 2), (17, 16, 3),
+                                                         (18, 8, 8)]]
+    gs += [graphgen.road(512, seed=4), graphgen.road(1024, seed=5),
+           graphgen.er(200_000, 800_000, seed=6), graphgen.er(60_000, 960_000, seed=7)]
+    gs += [graphgen.rgg(60_000, 3, 60.0, seed=9), graphgen.rgg(150_000, 3, 40.0, seed=10),
+           graphgen.rgg(300_000, 2, 16.0, seed=11), graphgen.lattice3(40, 6),
+           graphgen.rgg(1_000_000, 2, 16.0, seed=13), graphgen.rgg(50_000, 3, 90.0, seed=14),
+           graphgen.rgg(600_000, 2, 10.0, seed=15)]
+    return gs
+
+
 def mode_rules_leg(args, ctx):
     """Per-round mode rules on held-out graphs (the ten suite stand-ins at 5 %
-    scale), from forced-mode round times: the paper's H = 0.6 n, the byte
-    model's H (policy.BYTES_KAPPA), a threshold fitted to training graphs,
-    the learned switch trained on the same training graphs, and the
-    per-round best. Totals are summed round times (ns -> ms)."""
+    scale), from forced-mode round times of the default colouring: the
+    paper's H = 0.6 n, the byte model's H (policy.BYTES_KAPPA), a threshold
+    fitted to training graphs, the learned switch trained on the same
+    training graphs, and the per-round best. Totals are summed round times
+    (ns -> ms). Then whole colourings of the held-out graphs under the
+    threshold rule and under the learned switch (best of 3 each, CUDA events,
+    same colours checked). Returns (record, trained weights)."""
     import torch
 
-    from paper_1912_01478_gb300 import graphgen, policy
+    from paper_1912_01478_gb300 import graphgen, ipgc, policy
 
     if not args.mode_rules:
-        return None
-    train_specs = [(15, 16, 1), (16, 8, 2), (17, 16, 3), (18, 8, 8)]
-    train_graphs = [graphgen.rmat(a, b, seed=sd) for a, b, sd in train_specs]
-    train_graphs += [graphgen.road(512, seed=4), graphgen.road(1024, seed=5),
-                     graphgen.er(200_000, 800_000, seed=6), graphgen.er(60_000, 960_000, seed=7)]
-    train = policy.collect(ctx, train_graphs)
-    held = policy.collect(ctx, [graphgen.suite_graph(nm, 0.05) for nm in graphgen.SUITE])
+        return None, None
+    train = policy.collect(ctx, training_graphs())
+    held_graphs = [graphgen.suite_graph(nm, 0.05) for nm in graphgen.SUITE]
+    held = policy.collect(ctx, held_graphs)
     fit = policy.fit_threshold(train)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
     w, _ = policy.train(ctx, dev(train.x), dev(train.y), dev(train.w / max(train.w.mean(), 1e-9)),
@@ -315,10 +354,35 @@ def mode_rules_leg(args, ctx):
     out = {k: held.totals(v) / 1e6 for k, v in rules.items()}
     out["per_round_best"] = float(np.minimum(held.t_topo, held.t_data).sum() / 1e6)
     a, b, c = fit
-    return {"held_out": "the ten suite stand-ins at 5 % scale", "rounds": int(held.wl.size),
-            "total_round_ms": out, "byte_model_kappa": policy.BYTES_KAPPA,
-            "fitted": {"a_ns_per_node": a, "b_ns_per_wl": b, "c_ns": c,
-                       "H_over_n_at_1M": (a * 1e6 + c) / b / 1e6}}
+    # whole colourings: the threshold rule against the learned switch
+    policy.load(ctx, w)
+    real = {"threshold": 0.0, "learned": 0.0}
+    for rp, cl in held_graphs:
+        drp, dcl = torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda()
+        col = torch.empty(rp.size - 1, dtype=torch.int32, device="cuda")
+        ref = None
+        for mode in real:
+            o = ipgc.ColorOptions(mode=mode, validate=False)
+            ctx.color(drp, dcl, col, o)
+            ts = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.color(drp, dcl, col, o, wait=False)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            real[mode] += min(ts)
+            h = col.cpu().numpy()
+            if ref is None:
+                ref = h
+            elif not np.array_equal(ref, h):
+                raise SystemExit("the learned switch changed a colour")
+    policy.load(ctx, None)
+    return ({"held_out": "the ten suite stand-ins at 5 % scale", "rounds": int(held.wl.size),
+             "total_round_ms": out, "colouring_ms": real, "byte_model_kappa": policy.BYTES_KAPPA,
+             "fitted": {"a_ns_per_node": a, "b_ns_per_wl": b, "c_ns": c,
+                        "H_over_n_at_1M": (a * 1e6 + c) / b / 1e6}}, w)
 
 
 def micro_leg(args, ctx):
@@ -357,7 +421,7 @@ def micro_leg(args, ctx):
     return out
 
 
-def batched_leg(args, ctx, dev, stream):
+def batched_leg(args, ctx, dev, stream, policy_w=None):
     """Batched workload: G graphs (n log-uniform in [100, 200000], half
     Erdos-Renyi with average degree U(4, 32), half RMAT with edge factor 8,
     seed 4) coloured in one persistent launch with the autotuned schedule,
@@ -399,6 +463,16 @@ def batched_leg(args, ctx, dev, stream):
     _, st = batched.color_batched(ctx, no, eo, drp, dcl, out, opts, stream=stream)
     assert int(st["error"].max()) == 0
     batch_colors = out.clone()
+    ms_learned = None
+    if policy_w is not None:  # the same schedule, each round's mode from the learned switch
+        from paper_1912_01478_gb300 import policy
+
+        policy.load(ctx, policy_w)
+        ol = batched.BatchOptions.from_buffer_copy(opts)
+        ol.base.mode = ipgc.MODE_LEARNED
+        ms_learned = run(ol, args.batch_steps)
+        policy.load(ctx, None)
+        assert torch.equal(out, batch_colors), "the learned switch changed a colour"
 
     # plain path: one ipgc_color_ex launch per graph, same schedule, one stream
     plain = ipgc.ColorOptions(validate=False, t1=opts.base.t1, chunk=opts.base.chunk,
@@ -442,11 +516,86 @@ def batched_leg(args, ctx, dev, stream):
         "plain_graphs_per_s": G / (ms_plain / 1e3),
         "plain_ms": ms_plain,
         "speedup_vs_plain": ms_plain / ms_tuned,
+        "ms_learned": ms_learned,
+        "learned_speedup_vs_plain": ms_plain / ms_learned if ms_learned else None,
         "autotuned": batched.describe(opts),
         "autotune_sample_graphs": sample,
         "identical_colours_batched_vs_plain": True,
         "generation_s": round(gen_s, 1),
     }
+
+
+def road_leg(args, ctx, dev, stream, hbm):
+    """The road-network workload: a 4096 x 4096 4-neighbour grid, 30 % of the
+    edges deleted, 1 % long-range edges added (seed 3; 16.8 M nodes, 47.4 M
+    entries, the long tail of small rounds). Default options (no node is
+    above t1, so the rescanning kernel colours it), inputs resident; K timed
+    colourings (CUDA events) after W warm-ups; roofline as for the headline
+    (the paper's loop's bytes from one traced run)."""
+    import torch
+
+    from paper_1912_01478_gb300 import graphgen, ipgc
+
+    if not args.road:
+        return None
+    rp, cl = graphgen.workload("road_4096_seed3")
+    n, nnz = rp.size - 1, cl.size
+    drp = torch.from_numpy(rp).to(dev)
+    dcl = torch.from_numpy(cl).to(dev)
+    colors = torch.empty(n, dtype=torch.int32, device=dev)
+    opts = ipgc.ColorOptions(validate=False)
+    trace = ipgc.trace_buffer(n + 2, dev.index or 0)
+    fin = torch.zeros(n, dtype=torch.int32, device=dev)
+    _, st = ctx.color(drp, dcl, colors, opts, stream=stream, trace=trace, fin_round=fin)
+    tr = ipgc.read_trace(trace, st.rounds)
+    alg = algorithmic_bytes(rp, cl, fin.cpu().numpy(), tr["mode"].tolist())
+    del trace, fin
+    for _ in range(args.warmup):
+        ctx.color(drp, dcl, colors, opts, stream=stream, wait=False)
+    stream.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.color(drp, dcl, colors, opts, stream=stream, wait=False)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    st2 = ctx.last_stats()
+    assert st2.error == 0 and st2.rounds == st.rounds
+    avg = float(np.mean(ms))
+    gbs = alg / (avg / 1e3) / 1e9
+    return {"workload": "road 4096^2, 30 % deleted, 1 % long-range, seed 3", "n": int(n),
+            "nnz": int(nnz), "rounds": int(st.rounds), "colors": int(st.num_colors),
+            "ms": avg, "edges_per_s": nnz / (avg / 1e3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "algorithmic_bytes_per_step": int(alg)}}
+
+
+def validate_leg(ctx, drp, dcl, stream, opts_default):
+    """Device CSR check of the headline graph alone, and a default
+    ipgc_color_ex call (check included), CUDA events, best of 5."""
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc
+
+    def best(f):
+        f()
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    colors = torch.empty(drp.numel() - 1, dtype=torch.int32, device=drp.device)
+    v = best(lambda: ctx.validate(drp, dcl, stream=stream))
+    d = best(lambda: ctx.color(drp, dcl, colors, opts_default, stream=stream))
+    assert ctx.validate(drp, dcl, stream=stream) == ipgc.IPGC_OK
+    return v, d
 
 
 def dist_env():
@@ -634,22 +783,115 @@ def algorithmic_bytes(rp, cl, fin, modes):
     return total
 
 
-def cpu_baseline_leg():
-    import oracle
-    from paper_1912_01478_gb300 import graphgen
+def host_facts():
+    """The host's logical core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
 
-    rp, cl = graphgen.rmat(20, 16, seed=2)
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown",
+            "arch": platform.machine()}
+
+
+def _active_sums(fin, R, weights=None):
+    """x[r] = sum of weights over the nodes still active at round r (fin >= r)."""
+    c = np.bincount(fin, weights=weights, minlength=R + 2).astype(np.float64)
+    return np.cumsum(c[::-1])[::-1]
+
+
+def pushing_bytes(rp, cl, fin, modes, t1=64, chunk=1024, maxc_push=2048):
+    """Bytes the pushing kernel's own steps move in one colouring (a model of
+    its algorithm, not of its caches), from the per-node finalisation rounds:
+      degree pass   rowptr 4(n + 1) and the bitmaps cleared, 4 per word
+                    (ceil(min(d, 2048) / 32) words for d > t1);
+      round 1       rowptr, the first neighbour of each non-isolated node,
+                    colour and tentative-colour writes, loser pushes;
+      every commit  the node's row read once (4 d) with a check of each
+                    neighbour (rowptr pair and colour, 12 B), and a 4-byte
+                    atomic OR for each neighbour that keeps a bitmap and is
+                    still active;
+      round r >= 2  low-degree nodes (d <= t1) rescan their rows: 8 + 8 d +
+                    4 (assign) and 12 + 8 (lower neighbours) (detect);
+                    nodes above t1 read their bitmap (4 per word) and write
+                    tent (assign: 8 + 4 words + 4); nodes of one work item
+                    (d <= chunk) scan the lower part of their row, nodes of
+                    several scan their list of active lower-ID neighbours
+                    (8 per entry with its tentative colour; + 4 to write
+                    each list entry in round 2); commits, loser pushes and
+                    worklist reads (4n per phase when topology-driven)."""
+    n = rp.size - 1
+    deg = np.diff(rp).astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    lowmask = cl < src
+    nlow = np.bincount(src[lowmask], minlength=n).astype(np.int64)
+    R = int(fin.max())
+    big = deg > t1
+    words = np.where(big, (np.minimum(deg, maxc_push) + 31) // 32, 0)
+    total = 4.0 * (n + 1) + 4.0 * words.sum()                          # degree pass
+    A = _active_sums(fin, R)
+    total += 4 * (n + 1) + 4 * int((deg > 0).sum()) + 8 * n + 4 * A[2]  # round 1
+    # commits: row read once, neighbour checks, atomics to active bitmapped neighbours
+    total += 16.0 * deg.sum()
+    fs, fd = fin[src], fin[cl]
+    total += 4.0 * np.count_nonzero(big[cl] & (fd > fs))
+    # per-round sums over the active set
+    low = ~big
+    A_low = _active_sums(fin, R, low.astype(np.float64))
+    D_low = _active_sums(fin, R, np.where(low, deg, 0).astype(np.float64))
+    L_low = _active_sums(fin, R, np.where(low, nlow, 0).astype(np.float64))
+    A_big = _active_sums(fin, R, big.astype(np.float64))
+    W_big = _active_sums(fin, R, words.astype(np.float64))
+    row1 = big & (deg <= chunk)
+    L_row = _active_sums(fin, R, np.where(row1, nlow, 0).astype(np.float64))
+    listed = deg > chunk
+    e = lowmask & listed[src]
+    m = np.minimum(fs[e], fd[e])  # a list entry is active while both ends are
+    Ecnt = np.bincount(m, minlength=R + 2).astype(np.float64)
+    E = np.cumsum(Ecnt[::-1])[::-1]
+    for r in range(2, R + 1):
+        a, w = A[r], A[r] - A[r + 1]
+        x = a - w
+        assign = A_low[r] * 12 + 8 * D_low[r] + A_big[r] * 12 + 4 * W_big[r]
+        detect = A_low[r] * 12 + 8 * L_low[r] + A_big[r] * 4 + 8 * L_row[r] + 8 * E[r]
+        if r == 2:
+            detect += 4 * E[r]
+        sweep = 4 * n if modes[r - 1] == 1 else 4 * a
+        total += assign + detect + 4 * w + 4 * x + 2 * sweep
+    return int(total)
+
+
+def cpu_baseline_leg(rp, cl):
+    """The oracle, single-threaded, on the headline graph itself (one colouring)."""
+    import oracle
+
     t = time.perf_counter()
     oracle.color(rp, cl, trace=False)
     dt = time.perf_counter() - t
+    h = host_facts()
     return {
         "value": cl.size / dt,
         "unit": UNIT,
         "cores": 1,
         "kind": "oracle",
-        "sample": f"one oracle colouring of the RMAT scale-20 graph from the same generator "
-                  f"(edge factor 16, same a/b/c, seed 2; {rp.size - 1} nodes, {cl.size} entries): "
-                  f"{dt:.2f} s single-threaded",
+        "sample": f"one oracle colouring of the headline RMAT scale-22 graph, {dt:.1f} s on 1 core",
+        "host_nproc": h["nproc"],
+        "host_cpu": f"{h['arch']} {h['cpu_model']}",
         "seconds": dt,
     }
 
@@ -678,7 +920,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC + "; oracle sample: RMAT scale 18", "driver": "cpu oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_nproc": os.cpu_count(), "host_cpu": host_facts()["cpu_model"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -689,10 +932,6 @@ def main():
         run_reference(args)
         return
     rank, world, local = dist_env()
-    # the CPU baseline (oracle) runs before any GPU work
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_leg()
 
     import torch
 
@@ -708,6 +947,10 @@ def main():
 
     rp, cl = graphgen.workload(WORKLOAD)
     n, nnz = rp.size - 1, cl.size
+    # the CPU baseline (the oracle on this graph, one core) runs before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg(rp, cl)
     drp = torch.from_numpy(rp).to(dev)
     dcl = torch.from_numpy(cl).to(dev)
     colors = torch.empty(n, dtype=torch.int32, device=dev)
@@ -727,6 +970,10 @@ def main():
     rounds, ncolors, r0 = st.rounds, st.num_colors, st.filter_round
     fin_h = fin.cpu().numpy()
     alg_bytes = algorithmic_bytes(rp, cl, fin_h, tr["mode"].tolist())
+    maxdeg = int(np.diff(rp).max()) if n else 0
+    t1_used = maxdeg if maxdeg <= 255 else 64  # the library's rule when t1 = 0
+    own_bytes = (pushing_bytes(rp, cl, fin_h, tr["mode"].tolist(), t1=t1_used)
+                 if pushing and maxdeg > t1_used else alg_bytes)
     # per kernel: rounds before the hand-over round r0 and from it on, their
     # bytes and device times (%globaltimer of the trace)
     rb = round_bytes(rp, cl, fin_h, tr["mode"].tolist())
@@ -796,14 +1043,23 @@ def main():
     if rank != 0:
         dist.destroy_process_group()
         return
+    hbm, src = peaks()
+    validate_ms = default_ms = None
+    if world == 1:
+        validate_ms, default_ms = validate_leg(ctx, drp, dcl, stream, ipgc.ColorOptions(
+            mode=args.mode, driver=args.driver, forbidden=args.forbidden))
     worklist_out = worklist_leg(args, ctx, drp, dcl, stream) if world == 1 else None
+    rules_out, policy_w = mode_rules_leg(args, ctx) if world == 1 else (None, None)
     batched_out = None
     if world == 1 and args.batch_graphs > 0:
         del drp, dcl, colors
         torch.cuda.empty_cache()
-        batched_out = batched_leg(args, ctx, dev, stream)
+        batched_out = batched_leg(args, ctx, dev, stream, policy_w)
+    road_out = None
+    if world == 1:
+        torch.cuda.empty_cache()
+        road_out = road_leg(args, ctx, dev, stream, hbm)
     suite_out = suite_leg(args, ctx, stream) if world == 1 else None
-    rules_out = mode_rules_leg(args, ctx) if world == 1 else None
     micro_out = None
     if world == 1 and args.micro_n > 0:
         torch.cuda.empty_cache()
@@ -812,7 +1068,6 @@ def main():
     if world == 1 and args.serve_rates:
         torch.cuda.empty_cache()
         serving_out = serving_leg(args, ctx, dev, stream)
-    hbm, src = peaks()
     traffic = measured_traffic()
     avg_launch_s = float(np.mean(per_launch_ms)) / 1e3
     achieved_gbs = alg_bytes / avg_launch_s / 1e9
@@ -841,8 +1096,7 @@ def main():
             "schedule": f"{args.mode} (H = 0.6 n), driver {args.driver}",
             "forbidden_colours": ("bitmaps filled by pushes, lower-neighbour lists for conflicts"
                                   if pushing else "rows rescanned every round"),
-            "neighbour_filtering": ({"filter_degree": "default (1024)",
-                                     "start": "default (|WL| <= n/32)", "filter_round": int(r0)}
+            "neighbour_filtering": (f"filter_degree 1024, start |WL| <= n/32, round {int(r0)}"
                                     if not pushing else "off (pushing)"),
             "l2": "inputs larger than L2 (col 513 MB vs 129 MB L2); no flush",
             "parallelism": "replicas" if world > 1 else "single GPU",
@@ -856,10 +1110,10 @@ def main():
             "traffic": traffic,
             "peak_source": src,
             "algorithmic_bytes_per_step": int(alg_bytes),
+            "bytes_model": "the paper's loop (rows rescanned every round), exact from the trace",
             "avg_step_ms": avg_launch_s * 1e3,
             "kernels": " + ".join(k["kernel"] for k in per_kernel),
             "launches_per_step": launches_per_step,
-            "per_kernel": per_kernel,
             "traffic_source": "profiles/rmat_s22_dram_traffic.md (ncu dram__bytes_read.sum + "
                               "dram__bytes_write.sum, both launches, one colouring)"
                               if traffic is not None else "no ncu summary for these kernel sources",
@@ -873,16 +1127,98 @@ def main():
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clk.summary(),
         "cpu_baseline": ({k: v for k, v in cpu.items() if k != "seconds"} if cpu else None),
-        "batched": batched_out,
-        "serving": serving_out,
-        "micro_benchmark": micro_out,
-        "worklist_policy": worklist_out,
-        "suite": suite_out,
-        "mode_rules": rules_out,
+        "roofline_dram": ({"achieved": traffic / avg_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": traffic / avg_launch_s / 1e9 / hbm, "bytes_per_step": traffic,
+                           "what": "DRAM bytes the kernels move (ncu) / the same duration"}
+                          if traffic is not None else None),
+        "roofline_own": {"achieved": own_bytes / avg_launch_s / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": own_bytes / avg_launch_s / 1e9 / hbm,
+                         "bytes_per_step": int(own_bytes),
+                         "what": "the pushing kernel's own steps' bytes (pushing_bytes) / duration"},
+        "validate_ms": validate_ms,
+        "default_call_ms": default_ms,
+        "road": compact_road(road_out),
+        "batched": compact_batched(batched_out),
+        "serving": compact_serving(serving_out),
+        "mode_rules": compact_rules(rules_out),
+        "micro_benchmark": compact_micro(micro_out),
+        "worklist_policy": compact_worklist(worklist_out),
+        "suite": ({"geomean_hybrid_over_plain": suite_out["geomean_hybrid_over_plain"],
+                   "geomean_push_over_plain": suite_out["geomean_push_over_plain"]}
+                  if suite_out else None),
     }
-    print(json.dumps(out), flush=True)
+    if args.detail:
+        with open(args.detail, "w") as f:
+            json.dump({"headline_per_kernel": per_kernel, "batched": batched_out,
+                       "serving": serving_out, "micro_benchmark": micro_out,
+                       "worklist_policy": worklist_out, "suite": suite_out,
+                       "mode_rules": rules_out, "road": road_out}, f, indent=1)
+    print(json.dumps(out, separators=(",", ":")), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _r(x, k=4):
+    """x rounded to k significant digits (None stays None)."""
+    if x is None:
+        return None
+    return float(f"{x:.{k}g}")
+
+
+def compact_road(r):
+    if not r:
+        return None
+    return {"edges_per_s": _r(r["edges_per_s"]), "ms": _r(r["ms"]), "rounds": r["rounds"],
+            "frac": _r(r["roofline"]["frac"], 3)}
+
+
+def compact_batched(b):
+    if not b:
+        return None
+    out = {"graphs": b["graphs"], "graphs_per_s": _r(b["graphs_per_s"]),
+           "edges_per_s": _r(b["edges_per_s"]), "ms": _r(b["ms_per_batch"]),
+           "ms_default": _r(b["ms_per_batch_default_schedule"]),
+           "plain_graphs_per_s": _r(b["plain_graphs_per_s"]),
+           "speedup_vs_plain": _r(b["speedup_vs_plain"], 3),
+           "same_colours_as_plain": b["identical_colours_batched_vs_plain"],
+           "tuned": "{forbidden} t1={t1} chunk={chunk} team<={max_team}".format(**b["autotuned"])}
+    if b.get("ms_learned"):
+        out["ms_learned"] = _r(b["ms_learned"])
+        out["learned_speedup_vs_plain"] = _r(b["learned_speedup_vs_plain"], 3)
+    return out
+
+
+def compact_serving(s):
+    if not s:
+        return None
+    rates = s["rates"]
+    col = lambda k, d=3: [_r(r[k], d) for r in rates]  # noqa: E731
+    return {"rate_rps": [r["rate_rps"] for r in rates], "rps": col("throughput_rps"),
+            "p50_ms": col("p50_ms"), "p99_ms": col("p99_ms"), "plain_rps": col("plain_throughput_rps"),
+            "plain_p50_ms": col("plain_p50_ms"), "plain_p99_ms": col("plain_p99_ms"),
+            "plain_requests": [r["plain_requests"] for r in rates]}
+
+
+def compact_rules(m):
+    if not m:
+        return None
+    out = {k: _r(v) for k, v in m["total_round_ms"].items()}
+    out.update({f"colouring_{k}": _r(v) for k, v in m["colouring_ms"].items()})
+    return out
+
+
+def compact_micro(m):
+    if not m:
+        return None
+    return {"crossover_iteration": m["crossover_iteration"], "nowl_ms": _r(m["nowl"]["total_ms"]),
+            "wl_ms": _r(m["wl"]["total_ms"]), "hybrid_ms": _r(m["hybrid"]["total_ms"]),
+            "best_ms": _r(m["per_iteration_best_ms"])}
+
+
+def compact_worklist(w):
+    if not w:
+        return None
+    return {str(r["threshold_frac"]): [_r(r["keep"]["ms"]), _r(r["rebuild"]["ms"])] for r in w["rows"]}
 
 
 if __name__ == "__main__":
