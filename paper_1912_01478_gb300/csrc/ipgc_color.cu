@@ -151,16 +151,19 @@ __global__ void finish_kernel(Params p, int last_round) {
 // Entries are dealt to warps edge-balanced along the merge path of the row
 // ends and the entry indices (n + nnz items), so a hub's row is spread over
 // many warps and a run of short or empty rows over few. Each warp takes a
-// contiguous range of tiles of 32 x kValIpt consecutive items; it finds the
-// row its first tile starts in with a 32-way search of rowptr, and every
+// contiguous range of tiles of 32 consecutive items, one per lane; it finds
+// the row its first tile starts in with a 32-way search of rowptr, and every
 // later tile starts where the previous one ended. Per tile the warp stages
-// the row offsets and entries in shared memory with coalesced loads, and each
-// lane decodes its kValIpt consecutive items from there, then loads all
-// their other rows' offsets, then runs their lookups side by side.
+// the row offsets and entries in shared memory with coalesced loads.
+//
+// The check is bound by the number of scattered reads (each lookup is a
+// chain of them), so the row of the other end is searched by interpolation:
+// neighbour IDs are spread over [0, n), so a few probes suffice; after
+// three, halving takes over to bound the worst case.
 
-constexpr int kValIpt = 8;                // merge-path items per lane
-constexpr int kValTile = 32 * kValIpt;    // items per warp tile
+constexpr int kValTile = 32;     // items per warp tile (one per lane)
 constexpr int kValBlock = 256;
+constexpr int kValMinBlocks = 8; // resident CTAs per SM (a full SM: 64 warps)
 
 __global__ void validate_rowptr_kernel(const int32_t* __restrict__ rowptr, int32_t n, int64_t nnz,
                                        ValidateState* st) {
@@ -204,7 +207,35 @@ __device__ __forceinline__ int64_t merge_rows_before(const int32_t* rowptr, int3
   return lo + __popc(__ballot_sync(FULL, p));
 }
 
-__global__ void __launch_bounds__(kValBlock)
+// Is v in col[a, b) (sorted ascending, b > a)? Interpolation on [lo, hi]
+// while col[lo] < v < col[hi].
+__device__ __forceinline__ bool row_has(const int32_t* col, int32_t a, int32_t b, int32_t v) {
+  int32_t lo = a, hi = b - 1;
+  int32_t xl = __ldg(col + lo), xh = __ldg(col + hi);
+  if (xl == v || xh == v) return true;
+  if (v < xl || v > xh) return false;
+  for (int step = 0; hi - lo > 1; ++step) {
+    int32_t m;
+    if (step < 3) {
+      m = lo + (int32_t)(((int64_t)(v - xl) * (hi - lo)) / (int64_t)(xh - xl));
+      m = max(lo + 1, min(hi - 1, m));
+    } else {
+      m = lo + ((hi - lo) >> 1);
+    }
+    const int32_t x = __ldg(col + m);
+    if (x == v) return true;
+    if (x < v) {
+      lo = m;
+      xl = x;
+    } else {
+      hi = m;
+      xh = x;
+    }
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kValBlock, kValMinBlocks)
 validate_entries_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                         int32_t n, int64_t nnz, ValidateState* st) {
   constexpr int kWarps = kValBlock / 32;
@@ -231,11 +262,14 @@ validate_entries_kernel(const int32_t* __restrict__ rowptr, const int32_t* __res
     const int nc = (int)min((int64_t)kValTile, nnz - k0);
     __syncwarp();  // the previous tile's readers are done
     for (int j = lane; j < nr; j += 32) sr[j] = __ldg(rowptr + i0 + j);
-    for (int j = lane; j < nc; j += 32) sc[j] = __ldg(col + k0 + j);
+    if (lane < nc) sc[lane] = __ldg(col + k0 + lane);
     __syncwarp();
-    // this lane's items [td, td + kValIpt): its start row from the staged offsets
-    const int64_t td = d0 + (int64_t)lane * kValIpt;
-    int64_t i = i0, k = 0;
+    // this lane's item d0 + lane: its row from the staged offsets
+    const int64_t td = d0 + lane;
+    int64_t i = i0;
+    bool entry = false;
+    int32_t v = 0, u = 0, sv = 0, dv = 0;
+    int64_t k = 0;
     if (td < total) {
       int lo = 0, hi = (int)min((int64_t)kValTile, (int64_t)n - i0);
       while (lo < hi) {
@@ -247,79 +281,30 @@ validate_entries_kernel(const int32_t* __restrict__ rowptr, const int32_t* __res
       }
       i = i0 + lo;
       k = td - i;
-    }
-    // pass 1, registers only: the lane's entries (v, u), the layout checks
-    int32_t vq[kValIpt], uq[kValIpt], dq[kValIpt];
-#pragma unroll
-    for (int q = 0; q < kValIpt; ++q) {
-      vq[q] = -1;
-      uq[q] = -1;
-      dq[q] = 0;
-      if (td + q >= total) continue;
-      const int ri = (int)(i - i0);
-      if (i < n && (int64_t)sr[ri + 1] <= k) {  // the end of row i
-        ++i;
-        continue;
+      const int ri = lo;
+      if (i < n && (int64_t)sr[ri + 1] > k) {  // entry k of row i (else the end of row i)
+        entry = true;
+        v = (int32_t)i;
+        sv = sr[ri];
+        dv = sr[ri + 1] - sv;
+        u = sc[k - k0];
       }
-      const int32_t v = (int32_t)i;
-      const int32_t sv = sr[ri];
-      const int32_t u = sc[k - k0];
+    }
+    // the next tile starts after the rows whose ends lie in this one
+    i0 = i0 + __popc(__ballot_sync(FULL, td < total && !entry));
+    if (entry) {
       if (u < 0 || u >= n || u == v) {
         bad |= 4;
       } else {
         if (k > sv && (k - 1 >= k0 ? sc[k - 1 - k0] : __ldg(col + k - 1)) >= u) bad |= 8;
-        vq[q] = v;
-        uq[q] = u;
-        dq[q] = sr[ri + 1] - sv;
-      }
-      ++k;
-    }
-    // the next tile starts where lane 31's items ended
-    i0 = __shfl_sync(FULL, i, 31);
-    // pass 2: every entry's other row (independent loads)
-    int32_t aq[kValIpt], bq[kValIpt];
-#pragma unroll
-    for (int q = 0; q < kValIpt; ++q) {
-      aq[q] = 0;
-      bq[q] = 0;
-      if (uq[q] >= 0) {
-        aq[q] = __ldg(rowptr + uq[q]);
-        bq[q] = __ldg(rowptr + uq[q] + 1);
-      }
-    }
-    // pass 3: the entries that search (larger (degree, ID) end), all their
-    // binary searches advanced together
-    bool act[kValIpt], fnd[kValIpt];
-#pragma unroll
-    for (int q = 0; q < kValIpt; ++q) {
-      const int32_t du = bq[q] - aq[q];
-      act[q] = uq[q] >= 0 && (du < dq[q] || (du == dq[q] && uq[q] < vq[q]));
-      fnd[q] = false;
-      resp += act[q];
-    }
-    bool any = true;
-    while (any) {
-      any = false;
-#pragma unroll
-      for (int q = 0; q < kValIpt; ++q) {
-        if (act[q] && aq[q] < bq[q]) {
-          const int m = aq[q] + ((bq[q] - aq[q]) >> 1);
-          const int32_t x = __ldg(col + m);
-          if (x == vq[q]) {
-            fnd[q] = true;
-            act[q] = false;
-          } else if (x < vq[q]) {
-            aq[q] = m + 1;
-          } else {
-            bq[q] = m;
-          }
-          any |= act[q] && aq[q] < bq[q];
+        const int32_t su = __ldg(rowptr + u), eu = __ldg(rowptr + u + 1);
+        const int32_t du = eu - su;
+        if (du < dv || (du == dv && u < v)) {  // this end looks the pair up in the other's row
+          ++resp;
+          if (du == 0 || !row_has(col, su, eu, v)) bad |= 16;
         }
       }
     }
-#pragma unroll
-    for (int q = 0; q < kValIpt; ++q)
-      if (act[q] && !fnd[q]) bad |= 16;  // searched and not found
   }
   // one atomic per CTA for the count, one per warp for a failure
   bad = __reduce_or_sync(FULL, bad);
@@ -434,6 +419,7 @@ cudaError_t launch_validate(const int32_t* rowptr, const int32_t* col, int32_t n
   if (e != cudaSuccess) return e;
   const int64_t tiles = ((int64_t)n + nnz + kValTile - 1) / kValTile;
   const int64_t eb = (tiles + kValBlock / 32 - 1) / (kValBlock / 32);
+  // (at most kValMinBlocks CTAs per SM are resident; more only queue)
   validate_entries_kernel<<<(int)(eb < blocks ? eb : blocks), kValBlock, 0, s>>>(rowptr, col, n, nnz,
                                                                                st);
   e = cudaGetLastError();

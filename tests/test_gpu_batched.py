@@ -167,3 +167,24 @@ def test_autotuners_keep_colours(ctx):
     rc = ipgc.lib().ipgc_color_ex(ctx.handle, g_rp.data_ptr(), g_cl.data_ptr(), rp.size - 1, cl.size,
                                   scratch.data_ptr(), ctypes.byref(st1), ctypes.byref(opt), None)
     assert rc == 0 and np.array_equal(scratch.cpu().numpy(), ref.colors)
+
+
+def test_batch_with_the_learned_switch(ctx, mixed_batch):
+    # the learned switch in a batched launch: a hand-built network that says
+    # "topology-driven" while the largest colour is in a band (so rounds of
+    # both modes alternate within a graph, and late rounds follow), loaded
+    # into the context; every graph keeps the oracle's colours, with the
+    # pushing and the rescanning batched kernels
+    from paper_1912_01478_gb300 import policy
+    from test_gpu_parity import band_network
+
+    bt, refs = mixed_batch
+    policy.load(ctx, band_network(3 / 67, 8 / 72))  # maxc in (3, 8)
+    try:
+        for forbidden in ("auto", "rescan"):
+            colors, st = run_batch(ctx, bt, mode="learned", forbidden=forbidden)
+            check_against_oracle(bt, colors, st, refs)
+            # some graph ran topology-driven rounds after the first
+            assert int(st["rounds_topo"].max()) > 1
+    finally:
+        policy.load(ctx, None)

@@ -103,9 +103,14 @@ def test_adam_step_and_training(ctx):
     assert np.array_equal(w, w_again)
 
 
+# training and held-out graphs: RMAT, road grids, Erdos-Renyi, and 2-D and
+# 3-D random geometric graphs (mesh-like; regular, many rounds while most
+# nodes are active, where the best mode departs most from the threshold)
 TRAIN = [("rmat", 15, 16, 1), ("rmat", 16, 8, 2), ("rmat", 17, 16, 3), ("road", 512, 0, 4),
-         ("road", 1024, 0, 5), ("er", 200_000, 8, 6), ("er", 60_000, 32, 7), ("rmat", 18, 8, 8)]
-HELD = [("rmat", 16, 16, 21), ("rmat", 17, 8, 22), ("road", 768, 0, 23), ("er", 120_000, 16, 24)]
+         ("road", 1024, 0, 5), ("er", 200_000, 8, 6), ("er", 60_000, 32, 7), ("rmat", 18, 8, 8),
+         ("rgg3", 60_000, 60, 9), ("rgg2", 300_000, 16, 11), ("rgg3", 50_000, 90, 14)]
+HELD = [("rmat", 16, 16, 21), ("rmat", 17, 8, 22), ("road", 768, 0, 23), ("er", 120_000, 16, 24),
+        ("rgg3", 120_000, 80, 25)]
 
 
 def make(kind, a, b, seed):
@@ -113,6 +118,10 @@ def make(kind, a, b, seed):
         return graphgen.rmat(a, b, seed=seed)
     if kind == "road":
         return graphgen.road(a, seed=seed)
+    if kind == "rgg3":
+        return graphgen.rgg(a, 3, float(b), seed=seed)
+    if kind == "rgg2":
+        return graphgen.rgg(a, 2, float(b), seed=seed)
     return graphgen.er(a, a * b // 2, seed=seed)
 
 
@@ -135,8 +144,9 @@ def test_learned_policy_gain_and_parity(ctx):
     gain = t_thr / t_learned
     print(f"\nheld-out round time: threshold {t_thr/1e6:.3f} ms, learned {t_learned/1e6:.3f} ms "
           f"(gain {gain:.3f}x), all-data {t_data/1e6:.3f} ms, per-round best {t_best/1e6:.3f} ms")
-    # the trained network does not lose to the rule it falls back on
-    assert t_learned <= t_thr * 1.02
+    # the trained network beats the rule it falls back on, on graphs it was
+    # not trained on (summed round times of the default colouring's rounds)
+    assert t_learned < t_thr
     # colours under the learned policy are the oracle's, in both drivers
     policy.load(ctx, w)
     for rp, cl in held_graphs[:2]:
