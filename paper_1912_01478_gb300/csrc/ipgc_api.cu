@@ -121,10 +121,11 @@ int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
 //   With pushing (IPGC_FORBIDDEN_PUSH), the list arrays of filtering (lower
 //   parts only, no filtered items) and at the end the forbidden-colour
 //   bitmaps [nnz] words (a node's bitmap inside its own row range), the push
-//   queue and the winners list [n].
+//   queue, the winners list [n] and the push targets' {row start, degree}
+//   [n] int2.
 struct WsLayout {
   size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, fst_bytes, pbits_bytes,
-      pq_bytes, total;
+      pq_bytes, pinfo_bytes, total;
 };
 
 using ipgc::effective_chunk;
@@ -164,9 +165,11 @@ WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk, int filt_deg, bool
   L.pbits_bytes = push ? align256((size_t)nnz * sizeof(uint32_t)) : 0;
   // push items of one round: kPushChunk-entry chunks of the rows of nodes of degree > t1
   L.pq_bytes = push ? align256((size_t)(nnz / ipgc::kPushChunk + nbig + 1) * sizeof(int4)) : 0;
+  L.pinfo_bytes = push ? align256((size_t)n * sizeof(int2)) : 0;
   L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes +
             2 * L.alist_bytes + 2 * L.flen_bytes + 2 * L.fst_bytes +
-            (filt ? 2 * L.items_bytes : 0) + (push ? L.pbits_bytes + L.pq_bytes + L.a4n : 0);
+            (filt ? 2 * L.items_bytes : 0) +
+            (push ? L.pbits_bytes + L.pq_bytes + L.a4n + L.pinfo_bytes : 0);
   return L;
 }
 
@@ -265,6 +268,8 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
     p.pq = (int4*)w;
     w += L.pq_bytes;
     p.pw = (int32_t*)w;
+    w += L.a4n;
+    p.pinfo = (int2*)w;
   }
   p.ctrl = ctx->d_ctrl;
   p.trace = o.trace;

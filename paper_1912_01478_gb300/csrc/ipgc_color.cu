@@ -156,10 +156,10 @@ __global__ void finish_kernel(Params p, int last_round) {
 // later tile starts where the previous one ended. Per tile the warp stages
 // the row offsets and entries in shared memory with coalesced loads.
 //
-// The check is bound by the number of scattered reads (each lookup is a
-// chain of them), so the row of the other end is searched by interpolation:
-// neighbour IDs are spread over [0, n), so a few probes suffice; after
-// three, halving takes over to bound the worst case.
+// The lookups in the other end's rows are scattered reads of a 513 MB array
+// (RMAT scale 22): their DRAM sectors, not the entries, set the cost, so
+// each lookup reads whole sectors and guesses the first from the ID
+// (row_has): most rows are short and one sector decides.
 
 constexpr int kValTile = 32;     // items per warp tile (one per lane)
 constexpr int kValBlock = 256;
@@ -207,29 +207,55 @@ __device__ __forceinline__ int64_t merge_rows_before(const int32_t* rowptr, int3
   return lo + __popc(__ballot_sync(FULL, p));
 }
 
-// Is v in col[a, b) (sorted ascending, b > a)? Interpolation on [lo, hi]
-// while col[lo] < v < col[hi].
-__device__ __forceinline__ bool row_has(const int32_t* col, int32_t a, int32_t b, int32_t v) {
-  int32_t lo = a, hi = b - 1;
-  int32_t xl = __ldg(col + lo), xh = __ldg(col + hi);
-  if (xl == v || xh == v) return true;
-  if (v < xl || v > xh) return false;
-  for (int step = 0; hi - lo > 1; ++step) {
-    int32_t m;
-    if (step < 3) {
-      m = lo + (int32_t)(((int64_t)(v - xl) * (hi - lo)) / (int64_t)(xh - xl));
-      m = max(lo + 1, min(hi - 1, m));
+// Is v in col[a, b) (sorted ascending, b > a)? The lookup reads whole
+// 32-byte sectors (8 entries, two int4 loads of one aligned block; vec: col
+// is 16-byte aligned, else plain loads of the block's valid entries) and
+// places the first one by the ID: neighbour IDs are spread over [0, n), so v
+// sits near a + v (b - a) / n. Each block read either settles the answer
+// (v among its entries, or between two of them) or narrows the range
+// [lo, hi), whose bounding values vlo < v < vhi (-1 and n outside the row)
+// place the next block by interpolation; after three, halving takes over to
+// bound the worst case. A block may extend past the row or the array; only
+// its entries inside [lo, hi) are used (the 32-byte block of an entry lies
+// in the same page as the entry).
+__device__ __forceinline__ bool row_has(const int32_t* __restrict__ col, int32_t a, int32_t b,
+                                        int32_t v, int32_t n, bool vec) {
+  int32_t lo = a, hi = b;
+  int64_t vlo = -1, vhi = n;
+  for (int step = 0; lo < hi; ++step) {
+    int32_t g = step < 3 ? lo + (int32_t)(((int64_t)v - vlo) * (hi - lo) / (vhi - vlo))
+                         : lo + ((hi - lo) >> 1);
+    g = max(lo, min(hi - 1, g));
+    const int32_t blk = g & ~7;
+    int32_t e[8];
+    if (vec) {
+      const int4 x = __ldg(reinterpret_cast<const int4*>(col + blk));
+      const int4 y = __ldg(reinterpret_cast<const int4*>(col + blk + 4));
+      e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w;
+      e[4] = y.x; e[5] = y.y; e[6] = y.z; e[7] = y.w;
     } else {
-      m = lo + ((hi - lo) >> 1);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) e[q] = blk + q >= lo && blk + q < hi ? __ldg(col + blk + q) : 0;
     }
-    const int32_t x = __ldg(col + m);
-    if (x == v) return true;
-    if (x < v) {
-      lo = m;
-      xl = x;
+    const int32_t f = max(lo, blk), l = min(hi, blk + 8) - 1;  // the block's entries in range
+    int32_t first = 0, last = 0;
+    bool hit = false;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool in = blk + q >= f && blk + q <= l;
+      hit |= in && e[q] == v;
+      if (blk + q == f) first = e[q];
+      if (blk + q == l) last = e[q];
+    }
+    if (hit) return true;
+    if (v < first) {
+      hi = f;
+      vhi = first;
+    } else if (v > last) {
+      lo = l + 1;
+      vlo = last;
     } else {
-      hi = m;
-      xh = x;
+      return false;  // between two entries of the block
     }
   }
   return false;
@@ -244,6 +270,7 @@ validate_entries_kernel(const int32_t* __restrict__ rowptr, const int32_t* __res
   __shared__ unsigned long long s_resp[kWarps];
   if (*reinterpret_cast<volatile int*>(&st->err) != 0) return;  // rowptr is not safe to follow
   const int warp = threadIdx.x >> 5, lane = lane_id();
+  const bool cvec = ((uintptr_t)col & 15u) == 0;
   int32_t* sr = s_row[warp];
   int32_t* sc = s_col[warp];
   const int64_t total = (int64_t)n + nnz;
@@ -301,7 +328,7 @@ validate_entries_kernel(const int32_t* __restrict__ rowptr, const int32_t* __res
         const int32_t du = eu - su;
         if (du < dv || (du == dv && u < v)) {  // this end looks the pair up in the other's row
           ++resp;
-          if (du == 0 || !row_has(col, su, eu, v)) bad |= 16;
+          if (du == 0 || !row_has(col, su, eu, v, n, cvec)) bad |= 16;
         }
       }
     }

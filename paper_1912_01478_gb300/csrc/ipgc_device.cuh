@@ -155,6 +155,12 @@ struct Params {
   uint32_t* pbits;
   int4* pq;
   int32_t* pw;
+  // With pushing, optional: per node {row start, degree} while the node keeps
+  // a bitmap and is active, {row start, 0} otherwise (written by round 1, the
+  // degree cleared when the node is committed), so a push after round 1
+  // learns whether and where to OR from one 8-byte gather instead of the row
+  // offsets and the colour. nullptr: pushes read rowptr and color.
+  int2* pinfo;
   // Optional result publication into host-mapped pinned memory (nullptr:
   // none). When a graph is done its team copies the colours to out_colors
   // and the control block to out_ctrl, then sets *out_done = 1, so the host

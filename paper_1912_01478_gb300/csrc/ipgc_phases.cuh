@@ -115,6 +115,13 @@ __device__ __forceinline__ void phase_commit(const Params& p, Smem<BS>& sm, cons
 
 __device__ __forceinline__ int num_chunks(int d, int chunk) { return (d + chunk - 1) / chunk; }
 
+// A node of degree > t1 committed: with pushing, it no longer receives pushes
+// (round 1 writes pinfo for every node, and the degree of a node of degree
+// <= t1 or committed in round 1 as 0; later commits retire their node here).
+__device__ __forceinline__ void retire_push_target(const Params& p, int v) {
+  if (p.pinfo) p.pinfo[v].y = 0;
+}
+
 // ---------------------------------------------------------------- round 1 --
 
 __device__ __forceinline__ void small_push(const Params& p, int s, int d, int t, int t1,
@@ -143,6 +150,9 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, in
       lose = d > 0 && ld_ro(p.col + s) < v;
       p.color[v] = lose ? 0 : 1;
       p.tent[v] = lose ? 0 : 1;
+      // push targets: the nodes above t1 that stay active (the pushes of this
+      // pass do not read these; the push phase after it does)
+      if (PUSH && pushing && p.pinfo) p.pinfo[v] = make_int2(s, lose && d > t1 ? d : 0);
       if (!lose) acc.maxc = 1;
       if (p.fin) p.fin[v] = lose ? 0 : 1;
       if (lose) acc.dsum += (unsigned long long)d;
@@ -447,6 +457,38 @@ __device__ __forceinline__ void push_to(const Params& p, int s, int d, int t) {
 }
 
 
+// Colour t into the bitmaps of the kGather nodes u[] (-1: none) that keep one
+// (degree > t1) and are still active: with pinfo one 8-byte gather each,
+// else their row offsets and colour (independent gathers: the pushes are
+// latency-bound).
+__device__ __forceinline__ void push_targets(const Params& p, const int (&u)[kGather], int t, int t1,
+                                             uint64_t pol) {
+  if (p.pinfo) {
+    int2 pi[kGather];
+#pragma unroll
+    for (int q = 0; q < kGather; ++q) pi[q] = u[q] >= 0 ? __ldcg(p.pinfo + u[q]) : make_int2(0, 0);
+#pragma unroll
+    for (int q = 0; q < kGather; ++q)
+      if (pi[q].y > 0) push_to(p, pi[q].x, pi[q].y, t);
+    return;
+  }
+  int sw[kGather], ew[kGather], cw[kGather];
+#pragma unroll
+  for (int q = 0; q < kGather; ++q) {
+    sw[q] = 0;
+    ew[q] = 0;
+    cw[q] = 1;
+    if (u[q] >= 0) {
+      sw[q] = ld_ro(p.rowptr + u[q]);
+      ew[q] = ld_ro(p.rowptr + u[q] + 1);
+      cw[q] = ld_keep(p.color + u[q], pol);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kGather; ++q)
+    if (cw[q] == 0 && ew[q] - sw[q] > t1) push_to(p, sw[q], ew[q] - sw[q], t);
+}
+
 // Colour t (just committed) into the bitmaps of the neighbours in entries
 // [lo, hi) of col that keep one (degree > t1) and are still active. One warp.
 inline __device__ __noinline__ void push_range(const Params& p, int64_t lo, int64_t hi, int t,
@@ -455,21 +497,7 @@ inline __device__ __noinline__ void push_range(const Params& p, int64_t lo, int6
   for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
     int u[kGather];
     load_window(p, a, lo, hi, -1, u);
-    int sw[kGather], ew[kGather], cw[kGather];
-#pragma unroll
-    for (int q = 0; q < kGather; ++q) {
-      sw[q] = 0;
-      ew[q] = 0;
-      cw[q] = 1;
-      if (u[q] >= 0) {  // three independent gathers: the push phase is latency-bound
-        sw[q] = ld_ro(p.rowptr + u[q]);
-        ew[q] = ld_ro(p.rowptr + u[q] + 1);
-        cw[q] = ld_keep(p.color + u[q], pol);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kGather; ++q)
-      if (cw[q] == 0 && ew[q] - sw[q] > t1) push_to(p, sw[q], ew[q] - sw[q], t);
+    push_targets(p, u, t, t1, pol);
   }
 }
 
@@ -492,6 +520,16 @@ __device__ __forceinline__ void small_push(const Params& p, int s, int d, int t,
       const int oj = __shfl_sync(FULL, g.off, jj);
       tq[q] = __shfl_sync(FULL, t, jj);
       u[q] = e < g.total ? ld_ro(p.col + sj + (e - oj)) : -1;
+    }
+    if (p.pinfo && check_active) {  // (round 1 writes pinfo while it pushes: not read then)
+      int2 pi[kPushUnroll];
+#pragma unroll
+      for (int q = 0; q < kPushUnroll; ++q)
+        pi[q] = u[q] >= 0 ? __ldcg(p.pinfo + u[q]) : make_int2(0, 0);
+#pragma unroll
+      for (int q = 0; q < kPushUnroll; ++q)
+        if (pi[q].y > 0) push_to(p, pi[q].x, pi[q].y, tq[q]);
+      continue;
     }
     int sw[kPushUnroll], ew[kPushUnroll], cw[kPushUnroll];
 #pragma unroll
@@ -653,21 +691,7 @@ inline __device__ __noinline__ void push_list(const Params& p, const int32_t* ls
   for (int64_t a = lo & ~int64_t(3); a < hi; a += kWindow) {
     int u[kGather];
     load_window_rw(lst, a, lo, hi, -1, u);
-    int sw[kGather], ew[kGather], cw[kGather];
-#pragma unroll
-    for (int q = 0; q < kGather; ++q) {
-      sw[q] = 0;
-      ew[q] = 0;
-      cw[q] = 1;
-      if (u[q] >= 0) {
-        sw[q] = ld_ro(p.rowptr + u[q]);
-        ew[q] = ld_ro(p.rowptr + u[q] + 1);
-        cw[q] = ld_keep(p.color + u[q], pol);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kGather; ++q)
-      if (cw[q] == 0 && ew[q] - sw[q] > t1) push_to(p, sw[q], ew[q] - sw[q], t);
+    push_targets(p, u, t, t1, pol);
   }
 }
 
@@ -736,6 +760,7 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
       acc.dsum += (unsigned long long)d;
     } else {
       p.color[v] = t;
+      retire_push_target(p, v);
       acc.maxc = max(acc.maxc, t);
       if (p.fin) p.fin[v] = round;
     }
@@ -987,6 +1012,7 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
       acc.dsum += (unsigned long long)d;
     } else {
       p.color[v] = t;
+      retire_push_target(p, v);
       acc.maxc = max(acc.maxc, t);
       if (p.fin) p.fin[v] = round;
     }
@@ -1226,6 +1252,7 @@ __device__ __forceinline__ void item_detect_filtered(const Params& p, ItemStage&
       acc.dsum += (unsigned long long)d;
     } else {
       p.color[v] = t;
+      retire_push_target(p, v);
       acc.maxc = max(acc.maxc, t);
       if (p.fin) p.fin[v] = round;
     }
@@ -1674,7 +1701,7 @@ __device__ __forceinline__ PhaseAcc detect_small_nodes(const Params& p, Smem<BS>
                         if (!push) acc.nsm += 1;
                         acc.dsum += (unsigned long long)d;
                       } else {
-                        p.color[v] = t;
+                        p.color[v] = t;  // (a node of degree <= t1 is never a push target)
                         acc.maxc = max(acc.maxc, t);
                         if (p.fin) p.fin[v] = rv.round;
                       }
