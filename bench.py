@@ -127,9 +127,6 @@ def serving_leg(args, ctx, dev, stream):
         pick = np.where(rng.uniform(size=N) < 0.01, 512 + rng.integers(0, 4, N), rng.integers(0, 512, N))
         so = server.options(hbm_budget=24 << 30, host_budget=2 << 30, inflight=2,
                             max_batch_graphs=1024)
-        # teams of at most 64 CTAs: a large request (RMAT scale 20) then leaves
-        # most of its slot's CTAs to the small ones it shares a launch with
-        so.batch.max_team = 64
         srv = server.Server(dev.index or 0, so)
         lat = []
         done_n = [0]
@@ -202,7 +199,7 @@ def serving_leg(args, ctx, dev, stream):
     return {
         "workload": "Poisson arrivals per rate; graphs drawn from 512 graphs shaped like the batched "
                     "workload (seed 5) and, for 1 % of requests, 4 RMAT scale-20 edge-factor-16 graphs",
-        "server": "2 slots, teams of at most 64 CTAs, 24 GiB device arena",
+        "server": "2 slots, default teams (up to a whole slot), 24 GiB device arena",
         "seconds_per_rate": args.serve_seconds,
         "rates": out_rates,
     }
