@@ -998,8 +998,9 @@ def main():
         k["algorithmic_gbs"] = k["algorithmic_bytes"] / max(k["device_ms"], 1e-9) / 1e6
     if args.driver == "hostloop":  # round 1, two per later round, the finishing kernel
         launches_per_step = 2 + 2 * (rounds - 1)
-    elif pushing:  # the pushing kernel, then the rescanning one (returns at once)
-        launches_per_step = 2
+    elif pushing:  # the pushing kernel, then the rescanning ones (they return at once; the
+        # filtering kernel is enqueued too when the choice is automatic)
+        launches_per_step = 3 if args.forbidden == "auto" else 2
     else:  # the persistent kernel, then the filtering kernel (returns at once without a hand-over)
         launches_per_step = 2 if opts.filter_degree >= 0 else 1
     del trace, fin

@@ -158,13 +158,15 @@ typedef struct ipgc_options {
                              with several work items also keeps the list of its still-active
                              lower-ID neighbours for its conflict step. Same colours; 12 more
                              bytes of workspace per entry; needs the persistent driver
-                             (IPGC_ERR_UNSUPPORTED otherwise); turns neighbour filtering off;
+                             (IPGC_ERR_UNSUPPORTED otherwise); forced, it turns neighbour
+                             filtering off;
                              rounds that start with a colour above 2046 committed rescan; a
                              graph without a node of degree > t1 is coloured by rescanning.
                              IPGC_FORBIDDEN_AUTO (0, default): PUSH with the persistent driver
                              when the rows of the nodes of degree > t1 hold at least half of
                              the entries (checked on the device before round 1), else RESCAN
-                             (without neighbour filtering); RESCAN with the host-loop driver. */
+                             (with neighbour filtering as filter_degree says; the workspace
+                             holds what both need); RESCAN with the host-loop driver. */
 } ipgc_options;
 
 #define IPGC_WORKLIST_KEEP 0

@@ -139,8 +139,11 @@ bool effective_push(const ipgc_options& o) {
 
 // Degree above which a node is filtered (INT32_MAX: off); at least the
 // chunk, so every such node has several work items and a merge-state slot.
+// Forced pushing never filters; the automatic choice keeps filtering for the
+// graphs it leaves to the rescanning kernels (the pushing kernel ignores it).
 int effective_filt_deg(const ipgc_options& o) {
-  if (o.filter_degree < 0 || o.worklist == IPGC_WORKLIST_REBUILD || effective_push(o))
+  if (o.filter_degree < 0 || o.worklist == IPGC_WORKLIST_REBUILD ||
+      o.forbidden == IPGC_FORBIDDEN_PUSH)
     return INT32_MAX;
   const int f = o.filter_degree > 0 ? o.filter_degree : ipgc::kDefaultFiltDeg;
   const int lo = effective_chunk(o) > effective_t1(o) ? effective_chunk(o) : effective_t1(o);
