@@ -28,8 +28,8 @@ Also reported:
   clocks        nvidia-smi samples taken during the timed region;
   validate_ms   the device CSR check of the headline graph, and default_ms a
                 default ipgc_color_ex call (check included);
-  road          the road-network workload (4096^2 grid, seed 3): edges/s and
-                its roofline;
+  road, er      the road-network workload (4096^2 grid, seed 3): edges/s and
+                its roofline; the Erdos-Renyi workload (n = 10,000): edges/s;
   batched, serving, mode_rules: compact summaries of those legs (the full
                 records go to --detail FILE).
 
@@ -574,6 +574,33 @@ def road_leg(args, ctx, dev, stream, hbm):
                          "frac": gbs / hbm, "algorithmic_bytes_per_step": int(alg)}}
 
 
+def er_leg(args, ctx, dev, stream):
+    """The small Erdos-Renyi workload (n = 10,000, m = 40,000, seed 1):
+    K timed colourings after W warm-ups (CUDA events), default options
+    without the check."""
+    import torch
+
+    from paper_1912_01478_gb300 import graphgen, ipgc
+
+    rp, cl = graphgen.workload("er_n10000_deg8_seed1")
+    drp = torch.from_numpy(rp).to(dev)
+    dcl = torch.from_numpy(cl).to(dev)
+    colors = torch.empty(rp.size - 1, dtype=torch.int32, device=dev)
+    o = ipgc.ColorOptions(validate=False)
+    for _ in range(max(args.warmup, 3)):
+        _, st = ctx.color(drp, dcl, colors, o, stream=stream)
+    ms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.color(drp, dcl, colors, o, stream=stream, wait=False)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    avg = float(np.mean(ms))
+    return {"ms": _r(avg), "edges_per_s": _r(cl.size / (avg / 1e3)), "rounds": int(st.rounds)}
+
+
 def validate_leg(ctx, drp, dcl, stream, opts_default):
     """Device CSR check of the headline graph alone, and a default
     ipgc_color_ex call (check included), CUDA events, best of 5."""
@@ -1058,10 +1085,11 @@ def main():
         del drp, dcl, colors
         torch.cuda.empty_cache()
         batched_out = batched_leg(args, ctx, dev, stream, policy_w)
-    road_out = None
+    road_out = er_out = None
     if world == 1:
         torch.cuda.empty_cache()
         road_out = road_leg(args, ctx, dev, stream, hbm)
+        er_out = er_leg(args, ctx, dev, stream)
     suite_out = suite_leg(args, ctx, stream) if world == 1 else None
     micro_out = None
     if world == 1 and args.micro_n > 0:
@@ -1145,6 +1173,7 @@ def main():
                          "bytes_per_step": int(own_bytes), "what": "pushing_bytes"},
         "validate_ms": _r(validate_ms),
         "default_call_ms": _r(default_ms),
+        "er": er_out,
         "road": compact_road(road_out),
         "batched": compact_batched(batched_out),
         "serving": compact_serving(serving_out),
