@@ -104,7 +104,7 @@ def serving_leg(args, ctx, dev, stream):
     request at a time through ipgc_color_host (copies inside each call)."""
     import torch
 
-    from paper_1912_01478_gb300 import graphgen, server
+    from paper_1912_01478_gb300 import graphgen, ipgc, server
 
     rates = [int(r) for r in args.serve_rates.split(",") if r]
     if not rates:
@@ -127,6 +127,7 @@ def serving_leg(args, ctx, dev, stream):
         pick = np.where(rng.uniform(size=N) < 0.01, 512 + rng.integers(0, 4, N), rng.integers(0, 512, N))
         so = server.options(hbm_budget=24 << 30, host_budget=2 << 30, inflight=2,
                             max_batch_graphs=1024)
+        so.batch.base.forbidden = ipgc.FORBIDDEN[args.forbidden]
         srv = server.Server(dev.index or 0, so)
         lat = []
         done_n = [0]
@@ -199,7 +200,8 @@ def serving_leg(args, ctx, dev, stream):
     return {
         "workload": "Poisson arrivals per rate; graphs drawn from 512 graphs shaped like the batched "
                     "workload (seed 5) and, for 1 % of requests, 4 RMAT scale-20 edge-factor-16 graphs",
-        "server": "2 slots, default teams (up to a whole slot), 24 GiB device arena",
+        "server": "2 slots, default teams (up to a whole slot), 24 GiB device arena, forbidden "
+                  "colours: " + ("rows rescanned" if args.forbidden == "rescan" else "bitmaps"),
         "seconds_per_rate": args.serve_seconds,
         "rates": out_rates,
     }

@@ -333,9 +333,13 @@ IPGC_API int ipgc_batch_plan(int32_t num_graphs, const int32_t* n, const int64_t
  * the result into pinned staging and raises a host-visible flag), not when
  * its batch ends, and its device memory then admits the next requests at
  * once. Each result is the colouring the graph gets alone (the batched
- * phases). With batch.base.mode = IPGC_MODE_LEARNED the network loaded by
- * ipgc_server_policy_load chooses each round's mode (the threshold rule
- * without one, or where it is unsure).
+ * phases). Unless batch.base.forbidden is IPGC_FORBIDDEN_RESCAN, the
+ * launches colour with forbidden-colour bitmaps (see ipgc_options.forbidden;
+ * graphs without a node of degree > t1 rescan in the same launch), and each
+ * request's device memory holds its bitmaps and lists (about 12 more bytes
+ * per entry and 16 per node). With batch.base.mode = IPGC_MODE_LEARNED the
+ * network loaded by ipgc_server_policy_load chooses each round's mode (the
+ * threshold rule without one, or where it is unsure).
  */
 typedef struct ipgc_server ipgc_server;
 

@@ -166,8 +166,9 @@ WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk, int filt_deg, bool
   L.flen_bytes = lists ? align256((size_t)gcap * sizeof(int2)) : 0;
   L.fst_bytes = lists ? align256((size_t)gcap * sizeof(int32_t)) : 0;
   L.pbits_bytes = push ? align256((size_t)nnz * sizeof(uint32_t)) : 0;
-  // push items of one round: kPushChunk-entry chunks of the rows of nodes of degree > t1
-  L.pq_bytes = push ? align256((size_t)(nnz / ipgc::kPushChunk + nbig + 1) * sizeof(int4)) : 0;
+  // push items of one round: one-window items of the rows of nodes of degree > t1
+  // (ceil(d / kPushChunk) + 1 at most for a row of d entries)
+  L.pq_bytes = push ? align256((size_t)(nnz / ipgc::kPushChunk + 2 * nbig + 1) * sizeof(int4)) : 0;
   L.pinfo_bytes = push ? align256((size_t)n * sizeof(int2)) : 0;
   L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes +
             2 * L.alist_bytes + 2 * L.flen_bytes + 2 * L.fst_bytes +

@@ -197,6 +197,23 @@ void build_schedule(const Params* h_params, int32_t G, int grid, int max_team,
   *nsolo_out = (int32_t)solo.size();
 }
 
+namespace {
+
+// The kernel arguments of a schedule uploaded to d_lists (see build_schedule).
+BatchParams batch_params(const Params* d_params, int32_t* d_lists, int32_t njobs, int32_t nsolo,
+                         int grid) {
+  BatchParams bp;
+  bp.params = d_params;
+  bp.jobs = reinterpret_cast<const int4*>(d_lists);
+  bp.cta_off = d_lists + 4 * (size_t)njobs;
+  bp.solo_list = bp.cta_off + grid + 1;
+  bp.nsolo = nsolo;
+  bp.solo_next = d_lists + 4 * (size_t)njobs + grid + 1 + nsolo;
+  return bp;
+}
+
+}  // namespace
+
 cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid, bool cooperative,
                             const std::vector<int32_t>& lists, int32_t njobs, int32_t nsolo,
                             Params* d_params, int32_t* d_lists, cudaStream_t s, bool push) {
@@ -207,20 +224,14 @@ cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid,
     e = cudaMemcpyAsync(d_lists, lists.data(), sizeof(int32_t) * lists.size(),
                         cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
-  BatchParams bp;
-  bp.params = d_params;
-  bp.jobs = reinterpret_cast<const int4*>(d_lists);
-  bp.cta_off = d_lists + 4 * (size_t)njobs;
-  bp.solo_list = bp.cta_off + grid + 1;
-  bp.nsolo = nsolo;
-  bp.solo_next = d_lists + 4 * (size_t)njobs + grid + 1 + nsolo;
-  return launch_batched(bp, bs, grid, cooperative, s, push);
+  return launch_batched(batch_params(d_params, d_lists, njobs, nsolo, grid), bs, grid, cooperative,
+                        s, push);
 }
 
 cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int max_team,
                                 int64_t nnz_per_cta, bool cooperative, Params* d_params,
                                 int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,
-                                cudaStream_t s, int* rc) {
+                                cudaStream_t s, int* rc, bool push) {
   *rc = IPGC_OK;
   int32_t njobs = 0, nsolo = 0;
   build_schedule(h_params, G, grid, max_team, nnz_per_cta, lists, &njobs, &nsolo, nullptr);
@@ -228,8 +239,8 @@ cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int g
     *rc = IPGC_ERR_UNSUPPORTED;
     return cudaSuccess;
   }
-  return launch_schedule(h_params, G, bs, grid, cooperative, lists, njobs, nsolo, d_params,
-                         d_lists, s, false);
+  return launch_schedule(h_params, G, bs, grid, cooperative, lists, njobs, nsolo, d_params, d_lists,
+                         s, push);
 }
 
 }  // namespace ipgc
@@ -355,7 +366,7 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     if (nbig > n) nbig = n;
     item_base[g + 1] = item_base[g] + e / chunk + nbig + 1;
     gbase[g + 1] = gbase[g] + e / ((int64_t)chunk + 1) + 1;
-    pq_base[g + 1] = pq_base[g] + (push ? e / ipgc::kPushChunk + nbig + 1 : 0);
+    pq_base[g + 1] = pq_base[g] + (push ? e / ipgc::kPushChunk + 2 * nbig + 1 : 0);
     // lists are read as int4 windows from their buffer's base: every graph's
     // slice starts on a 16-byte boundary
     lbase[g + 1] = lbase[g] + (push ? (e + 3) / 4 * 4 : 0);
@@ -396,9 +407,11 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   const size_t b_gpint = push ? b_gint : 0;
   const size_t b_pq = al256(sizeof(int4) * (size_t)pq_base[num_graphs]);
   const size_t b_pw = push ? b_node : 0;
+  // ... and per node {row start, degree while active and bitmapped} (push targets)
+  const size_t b_pinfo = push ? al256(sizeof(int2) * (size_t)total_n) : 0;
   const size_t need = b_params + b_lists + b_plists + b_ctrl + 3 * b_node + 3 * b_items + b_gbits +
                       3 * b_gint + b_edge + 2 * b_lists_e + 2 * b_gint2 + 2 * b_gpint + b_pq +
-                      b_pw + 256;
+                      b_pw + b_pinfo + 256;
   if (W->dev_bytes < need || W->device != dev) {
     if (W->dev) cudaFree(W->dev);
     W->dev = nullptr;
@@ -462,6 +475,8 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   w += b_pq;
   int32_t* d_pw = (int32_t*)w;
   w += b_pw;
+  int2* d_pinfo = (int2*)w;
+  w += b_pinfo;
   ipgc::ValidateState* d_err = (ipgc::ValidateState*)w;
 
   // optional validation of every graph (one launch per graph)
@@ -521,6 +536,7 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
       p.fdead = d_fdead + gbase[g];
       p.pq = d_pq + pq_base[g];
       p.pw = d_pw + node_off[g];
+      p.pinfo = d_pinfo + node_off[g];
     }
   }
 

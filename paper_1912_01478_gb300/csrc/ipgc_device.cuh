@@ -37,6 +37,13 @@ constexpr int kStageItems = 32;  // per-warp staging of work-item pushes
 constexpr int kPushMaxC = 32 * kGWords;  // forbidden-colour bitmaps hold colours 1..2048
 constexpr int kPushChunk = 128;  // row entries per queued push item (one warp window)
 
+// A committed row of d entries from s is pushed in items of one aligned
+// window each: item j covers entries [max(s, a), min(s + d, a + kPushChunk))
+// with a = (s & ~3) + j * kPushChunk (at most ceil(d / kPushChunk) + 1 items).
+__device__ __forceinline__ int push_items_of(int s, int d) {
+  return ((s & 3) + d + kPushChunk - 1) / kPushChunk;
+}
+
 // State of the CSR check (launch_validate): the failed checks' bits (cleared
 // by the caller) and the count of entries whose reverse was searched (reset by
 // the check's last launch).
@@ -135,6 +142,8 @@ struct Params {
   int32_t t1_auto;    // choose t1 on the device: the largest degree if <= kMaxT1, else t1
   int32_t push_auto;  // pushing kernel: colour with bitmaps only when the rows of degree > t1
                       // hold at least half of the entries (else leave it to rescanning)
+  int32_t push_stay;  // pushing kernel: a graph it would leave to the rescanning kernel is
+                      // coloured here by rescanning (the server runs one kernel per launch)
   int64_t handoff_wl; // hand over when |WL| <= handoff_wl (0: never)
   // Forbidden-colour bitmaps (pbits == nullptr: off). A node v of degree
   // d > t1 keeps the colours of its finalised neighbours as a bitmap of
@@ -143,7 +152,7 @@ struct Params {
   // its colour into the bitmaps of its neighbours when it is committed, so
   // the assignment step of v reads the bitmap instead of the row. The
   // conflict step lists its winners (pw: nodes of degree <= t1; pq: the
-  // kPushChunk-entry chunks {row start, degree, colour, chunk} of the rows of
+  // one-window items {row start, degree, colour, window} of the rows of
   // the others), and a push phase of the whole team follows it. A node with
   // several items also keeps the list of its lower-ID neighbours that are
   // still active (alist/flen/fst/fdead as for neighbour filtering, lower

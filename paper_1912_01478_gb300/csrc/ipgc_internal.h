@@ -50,10 +50,12 @@ void build_schedule(const Params* h_params, int32_t G, int grid, int max_team,
 cudaError_t launch_schedule(const Params* h_params, int32_t G, int bs, int grid, bool cooperative,
                             const std::vector<int32_t>& lists, int32_t njobs, int32_t nsolo,
                             Params* d_params, int32_t* d_lists, cudaStream_t s, bool push = false);
+// With `push` the pushing kernel runs the schedule (graphs it would leave to
+// the rescanning kernel need Params::push_stay).
 cudaError_t schedule_and_launch(const Params* h_params, int32_t G, int bs, int grid, int max_team,
                                 int64_t nnz_per_cta, bool cooperative, Params* d_params,
                                 int32_t* d_lists, size_t lists_cap, std::vector<int32_t>& lists,
-                                cudaStream_t s, int* rc);
+                                cudaStream_t s, int* rc, bool push = false);
 // Upper bound on the list length build_schedule makes for G graphs with
 // teams of at most kmax CTAs each on `grid` CTAs.
 inline size_t schedule_lists_bound(int32_t G, int grid, int kmax) {

@@ -191,7 +191,7 @@ __device__ void round1(const Params& p, Smem<BS>& sm, PhaseAcc& acc, Team tm, in
       const bool win = valid && !lose;
       small_push(p, s, win && !big ? d : 0, 1, t1, false);
       // the others' rows: queued for the push phase after round 1, one lane at a time
-      const int nq = win && big ? num_chunks(d, kPushChunk) : 0;
+      const int nq = win && big ? push_items_of(s, d) : 0;
       int incl = nq;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -431,6 +431,8 @@ __device__ __forceinline__ void prefetch_l2(const Params& p, int64_t lo, int64_t
 
 __device__ __forceinline__ int push_words(int d) { return (min(d, kPushMaxC) + 31) >> 5; }
 
+static_assert(kPushChunk == kWindow, "a push item is one window");
+
 constexpr int kPushUnroll = 8;
 
 // OR `bit` into bitmap word *w unless the word, as this SM's L1 may hold it,
@@ -499,6 +501,13 @@ inline __device__ __noinline__ void push_range(const Params& p, int64_t lo, int6
     load_window(p, a, lo, hi, -1, u);
     push_targets(p, u, t, t1, pol);
   }
+}
+
+// The window of queued push item it = {row start, degree, colour, j}
+// (push_items_of): its entries, -1 outside the row. One warp.
+__device__ __forceinline__ void load_push_item(const Params& p, int4 it, int (&u)[kGather]) {
+  const int64_t s = it.x, a = (s & ~int64_t(3)) + (int64_t)it.w * kPushChunk;
+  load_window(p, a, a > s ? a : s, min(s + it.y, a + kPushChunk), -1, u);
 }
 
 // The same for the 32 nodes of a warp, one per lane (colour t, entries
@@ -668,11 +677,11 @@ __device__ __forceinline__ void item_assign_push(const Params& p, int v, int s, 
 }
 
 // The row of a node of degree d (entries from s) committed with colour t,
-// queued for the push phase in kPushChunk-entry items {s, d, t, chunk}, and
-// asked into L2 meanwhile. One warp, warp-uniform arguments.
+// queued for the push phase in one-window items {s, d, t, j} (push_items_of),
+// and asked into L2 meanwhile. One warp, warp-uniform arguments.
 __device__ __forceinline__ void push_queue(const Params& p, int s, int d, int t) {
   const int lane = lane_id();
-  const int n = num_chunks(d, kPushChunk);
+  const int n = push_items_of(s, d);
   int base = 0;
   if (lane == 0) {
     base = atomicAdd(&p.ctrl->pqcnt, n);
@@ -1789,31 +1798,63 @@ __device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
 
 // The push phase that follows a conflict step (or round 1) with pushing:
 // the colours of the nodes committed in it into their active neighbours'
-// bitmaps. Work units: the queued kPushChunk-entry chunks of the rows of
-// winners of degree > t1 (one warp each), then the listed low-degree
-// winners 32 at a time (their rows laid end to end, at most 32 * t1
-// entries). A team barrier follows.
+// bitmaps. Work units: the queued one-window items of the rows of winners of
+// degree > t1 (one warp each; a warp loads its next item's window and the
+// record after that before it pushes the current one, so their latency
+// overlaps the pushes' gathers), then the listed low-degree winners 32 at a
+// time (their rows laid end to end, at most 32 * t1 entries). A team
+// barrier follows.
 template <int BS>
 __device__ __noinline__ void push_phase(const Params& p, int nq, int nw, int t1, Team tm) {
   const int gwarp = tm.cta * (BS / 32) + (threadIdx.x >> 5), nwarps = tm.ncta * (BS / 32);
   const int lane = lane_id();
   const int units = nq + (nw + 31) / 32;
-  for (int k = gwarp; k < units; k += nwarps) {
-    if (k < nq) {
-      const int4 it = ld_cg4(p.pq + k);  // {row start, degree, colour, chunk}
-      const int64_t lo = (int64_t)it.x + (int64_t)it.w * kPushChunk;
-      const int64_t hi = min((int64_t)it.x + it.y, lo + kPushChunk);
-      push_range(p, lo, hi, it.z, t1);
-    } else {
-      const int i = (k - nq) * 32 + lane;
-      int s = 0, d = 0, t = 1;
-      if (i < nw) {
-        const int v = ld_cg(p.pw + i);
-        s = ld_ro(p.rowptr + v);
-        d = ld_ro(p.rowptr + v + 1) - s;
-        t = ld_cg(p.color + v);
+  int k = gwarp;
+  if (k < nq) {
+    const uint64_t pol = l2_keep_policy();
+    const int4 none = make_int4(0, 0, 0, 0);
+    int4 A = ld_cg4(p.pq + k);
+    int4 B = k + nwarps < nq ? ld_cg4(p.pq + k + nwarps) : none;
+    int u[kGather];
+    load_push_item(p, A, u);
+    for (; k < nq; k += nwarps) {
+      const bool more = k + nwarps < nq;
+      const int4 C = k + 2 * nwarps < nq ? ld_cg4(p.pq + k + 2 * nwarps) : none;
+      int un[kGather];
+      if (more) load_push_item(p, B, un);
+      push_targets(p, u, A.z, t1, pol);
+      if (more) {
+#pragma unroll
+        for (int q = 0; q < kGather; ++q) u[q] = un[q];
       }
+      A = B;
+      B = C;
+    }
+  }
+  // the low-degree winners: the next share's rows are located while the
+  // current share pushes
+  auto locate = [&](int kk, int& s, int& d, int& t) {
+    const int i = (kk - nq) * 32 + lane;
+    s = 0;
+    d = 0;
+    t = 1;
+    if (kk < units && i < nw) {
+      const int v = ld_cg(p.pw + i);
+      s = ld_ro(p.rowptr + v);
+      d = ld_ro(p.rowptr + v + 1) - s;
+      t = ld_cg(p.color + v);
+    }
+  };
+  if (k < units) {
+    int s, d, t;
+    locate(k, s, d, t);
+    for (; k < units; k += nwarps) {
+      int sn, dn, tn;
+      locate(k + nwarps, sn, dn, tn);
       small_push(p, s, d, t, t1, true);
+      s = sn;
+      d = dn;
+      t = tn;
     }
   }
 }
@@ -2052,7 +2093,7 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
     if (pushing && p.push_auto)
       pushing = 2 * __ldcg(&c->bigsum) >= (unsigned long long)p.nnz;
   }
-  if (PUSH && !pushing) {  // every node on the low-degree path: nothing to push
+  if (PUSH && !pushing && !p.push_stay) {  // nothing to push: the rescanning kernel colours it
     if (lead) c->push_off = 1;
     return;
   }

@@ -17,7 +17,11 @@
 //
 // Batches run as ordinary launches of at most 1/inflight of the device's
 // resident CTAs each, so all CTAs of every in-flight batch fit on the GPU at
-// the same time and the bounded team barriers always complete.
+// the same time and the bounded team barriers always complete. Unless
+// rescanning is asked for, every launch runs the pushing batched kernel
+// (forbidden-colour bitmaps, as ipgc_color_batched), which also colours, by
+// rescanning, the graphs without a node above t1: one kernel per launch, so
+// a small request never waits for another kernel of its launch.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -128,13 +132,18 @@ struct Slot {
   std::vector<char> finished;  // ticket i already completed from its flag
 };
 
-// Per-request device layout (offsets from the request's block).
+// Per-request device layout (offsets from the request's block); with
+// pushing also the bitmaps, the two list buffers, the list counts and state,
+// the push queue, the winners and the push targets (offsets 0 without).
 struct DevLayout {
-  size_t rowptr, col, colors, tent, wl0, wl1, it0, it1, its, gbits, done_a, done_d, flag, total;
+  size_t rowptr, col, colors, tent, wl0, wl1, it0, it1, its, gbits, done_a, done_d, flag;
+  size_t pbits = 0, alist0 = 0, alist1 = 0, flen0 = 0, flen1 = 0, fst = 0, fdead = 0, pq = 0,
+         pw = 0, pinfo = 0;
+  size_t total;
   int64_t icap, gcap;
 };
 
-DevLayout dev_layout(int32_t n, int64_t nnz, int t1, int chunk) {
+DevLayout dev_layout(int32_t n, int64_t nnz, int t1, int chunk, bool push) {
   DevLayout L;
   int64_t nbig = nnz / (t1 + 1);
   if (nbig > n) nbig = n;
@@ -159,6 +168,19 @@ DevLayout dev_layout(int32_t n, int64_t nnz, int t1, int chunk) {
   L.done_a = take(4 * (size_t)L.gcap);
   L.done_d = take(4 * (size_t)L.gcap);
   L.flag = take(4 * (size_t)L.gcap);
+  if (push) {  // as the batched workspace: 12 bytes per entry, 16 per node, ...
+    const size_t e = (size_t)(nnz > 0 ? nnz : 1);
+    L.pbits = take(4 * e);
+    L.alist0 = take(4 * e);
+    L.alist1 = take(4 * e);
+    L.flen0 = take(8 * (size_t)L.gcap);
+    L.flen1 = take(8 * (size_t)L.gcap);
+    L.fst = take(4 * (size_t)L.gcap);
+    L.fdead = take(4 * (size_t)L.gcap);
+    L.pq = take(16 * (size_t)(nnz / ipgc::kPushChunk + 2 * nbig + 1));
+    L.pw = take(4 * (size_t)n);
+    L.pinfo = take(8 * (size_t)n);
+  }
   L.total = o;
   return L;
 }
@@ -173,6 +195,7 @@ struct ipgc_server {
   int device = 0;
   ipgc_server_options opt{};
   int t1 = 0, chunk = 0, bs = 256, grid = 0, max_team = 1;
+  bool push = false;  // forbidden-colour bitmaps: every launch runs the pushing batched kernel
   char* d_arena = nullptr;
   char* h_arena = nullptr;  // pinned
   char* m_arena = nullptr;  // h_arena's device mapping
@@ -273,7 +296,7 @@ bool admit_locked(ipgc_server* S) {
     size_t off = 0;
     if (!S->dev.alloc(r.d_bytes, &off)) break;
     r.d_off = off;
-    const DevLayout L = dev_layout(r.n, r.nnz, S->t1, S->chunk);
+    const DevLayout L = dev_layout(r.n, r.nnz, S->t1, S->chunk, S->push);
     char* dbase = S->d_arena + off;
     const char* hbase = S->h_arena + r.h_off;
     const void* src_rp = r.ref_rowptr ? (const void*)r.ref_rowptr : (const void*)hbase;
@@ -320,7 +343,7 @@ bool launch_locked(ipgc_server* S) {
   for (int32_t i = 0; i < G; ++i) {
     Request& r = S->reqs[sl->tickets[i]];
     r.st = St::Running;
-    const DevLayout L = dev_layout(r.n, r.nnz, S->t1, S->chunk);
+    const DevLayout L = dev_layout(r.n, r.nnz, S->t1, S->chunk, S->push);
     char* b = S->d_arena + r.d_off;
     Params& p = sl->params[i];
     std::memset(&p, 0, sizeof(p));
@@ -355,6 +378,19 @@ bool launch_locked(ipgc_server* S) {
     p.out_colors = (int32_t*)(S->m_arena + r.h_off + r.h_colors);
     p.out_ctrl = sl->m_ctrl + i;
     p.out_done = sl->m_done + i;
+    if (S->push) {  // a graph's bitmaps and lists, in its own block
+      p.push_stay = 1;  // one kernel per launch: graphs without bitmaps rescan in it
+      p.pbits = (uint32_t*)(b + L.pbits);
+      p.alist[0] = (int32_t*)(b + L.alist0);
+      p.alist[1] = (int32_t*)(b + L.alist1);
+      p.flen[0] = (int2*)(b + L.flen0);
+      p.flen[1] = (int2*)(b + L.flen1);
+      p.fst = (int32_t*)(b + L.fst);
+      p.fdead = (int32_t*)(b + L.fdead);
+      p.pq = (int4*)(b + L.pq);
+      p.pw = (int32_t*)(b + L.pw);
+      p.pinfo = (int2*)(b + L.pinfo);
+    }
   }
   int rc = IPGC_OK;
   cudaError_t e = cudaEventRecord(copied, S->copy_stream);
@@ -363,7 +399,7 @@ bool launch_locked(ipgc_server* S) {
   if (e == cudaSuccess)
     e = ipgc::schedule_and_launch(sl->params.data(), G, S->bs, S->grid, S->max_team,
                                   S->opt.batch.nnz_per_cta, false, sl->d_params, sl->d_lists,
-                                  sl->lists_cap, sl->lists, sl->stream, &rc);
+                                  sl->lists_cap, sl->lists, sl->stream, &rc, S->push);
   if (e == cudaSuccess) e = cudaEventRecord(sl->done, sl->stream);
   cudaEventDestroy(copied);
   if (e != cudaSuccess || rc != IPGC_OK) {
@@ -444,7 +480,8 @@ int ipgc_server_create(ipgc_server** out, int device, const ipgc_server_options*
     ipgc_server_options_default(&o);
   if (o.inflight < 1 || o.inflight > 8 || o.max_batch_graphs < 1 || o.max_pending < 1 ||
       o.hbm_budget < 4096 || o.host_budget < 4096 || o.batch.max_team < 0 ||
-      o.batch.nnz_per_cta < 1)
+      o.batch.nnz_per_cta < 1 || o.batch.base.forbidden < IPGC_FORBIDDEN_AUTO ||
+      o.batch.base.forbidden > IPGC_FORBIDDEN_PUSH)
     return IPGC_ERR_INVALID;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return IPGC_ERR_INVALID;
@@ -456,11 +493,16 @@ int ipgc_server_create(ipgc_server** out, int device, const ipgc_server_options*
   S->t1 = ipgc::effective_t1(o.batch.base);
   S->chunk = ipgc::effective_chunk(o.batch.base);
   S->bs = o.batch.base.block_size ? o.batch.base.block_size : ipgc::kBlock;
-  int occ = 0, sms = 0;
+  S->push = o.batch.base.forbidden != IPGC_FORBIDDEN_RESCAN;
+  int occ = 0, pocc = 0, sms = 0;
   int rc = IPGC_OK;
   if (ipgc::occupancy_batched(S->bs, &occ) != cudaSuccess ||
+      (S->push && ipgc::occupancy_batched(S->bs, &pocc, true) != cudaSuccess) ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     rc = IPGC_ERR_CUDA;
+  // with pushing every launch runs the pushing kernel (graphs without a node
+  // above t1 rescan inside it), whose occupancy sizes the slots
+  if (S->push) occ = pocc;
   S->grid = occ * sms / o.inflight;
   // largest team: max_team (0: the grid), at most the grid
   S->max_team = o.batch.max_team > 0 && o.batch.max_team < S->grid ? o.batch.max_team : S->grid;
@@ -522,7 +564,7 @@ int submit_impl(ipgc_server* S, const int32_t* h_rowptr, const int32_t* h_col, i
       ipgc_validate_csr(nullptr, h_rowptr, h_col, n, nnz, 0, nullptr) != IPGC_OK)
     return IPGC_ERR_INVALID;
   const size_t hb = by_ref ? al256(4 * (size_t)(n > 0 ? n : 1)) : host_bytes(n, nnz);
-  const size_t db = dev_layout(n, nnz, S->t1, S->chunk).total;
+  const size_t db = dev_layout(n, nnz, S->t1, S->chunk, S->push).total;
   if (hb > S->host.cap() || db > S->dev.cap()) return IPGC_ERR_TOO_LARGE;
   size_t h_off = 0;
   uint64_t t = 0;

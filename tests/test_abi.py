@@ -172,6 +172,22 @@ def test_ctx_create_reports_no_device_without_crash(lib):
     assert not h.value
 
 
+def test_server_options_checked_before_any_device_call(lib):
+    # bad options are refused before the device is touched (no GPU needed):
+    # the forbidden-colour source must be one of the three
+    from paper_1912_01478_gb300 import server
+
+    for bad in (-1, 3):
+        o = server.options()
+        o.batch.base.forbidden = bad
+        h = ctypes.c_void_p()
+        assert lib.ipgc_server_create(ctypes.byref(h), 0, ctypes.byref(o)) == ipgc.IPGC_ERR_INVALID
+        assert not h.value
+    o = server.options(inflight=0)
+    h = ctypes.c_void_p()
+    assert lib.ipgc_server_create(ctypes.byref(h), 0, ctypes.byref(o)) == ipgc.IPGC_ERR_INVALID
+
+
 # ------------------------------------------------ the generator library --
 
 def declared_generator_symbols():

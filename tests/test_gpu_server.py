@@ -1,5 +1,6 @@
 """Colouring server: continuous batching gives every request the colouring
-it gets alone (the CPU oracle's), whatever else is in flight; admission by
+it gets alone (the CPU oracle's), whatever else is in flight, with
+forbidden-colour bitmaps (the default) and with rescanning; admission by
 device memory, slot reuse, errors."""
 import threading
 import time
@@ -33,12 +34,18 @@ def check(res, ref):
     assert lat > 0
 
 
-def test_results_same_alone_and_in_the_mix(graphs):
-    from paper_1912_01478_gb300 import _build, server
+@pytest.mark.parametrize("forbidden", ["auto", "rescan"])
+def test_results_same_alone_and_in_the_mix(graphs, forbidden):
+    # the default server colours with forbidden-colour bitmaps (graphs
+    # without a node above t1 rescan in the same launch); "rescan" rereads
+    # rows in every launch
+    from paper_1912_01478_gb300 import _build, ipgc, server
 
     _build.build()
     gs, refs = graphs
-    srv = server.Server(0, server.options(inflight=2, max_batch_graphs=8))
+    o = server.options(inflight=2, max_batch_graphs=8)
+    o.batch.base.forbidden = ipgc.FORBIDDEN[forbidden]
+    srv = server.Server(0, o)
     # alone: one request at a time
     alone = []
     for rp, cl in gs[:6]:
