@@ -469,9 +469,17 @@ __device__ __forceinline__ void push_targets(const Params& p, const int (&u)[kGa
     int2 pi[kGather];
 #pragma unroll
     for (int q = 0; q < kGather; ++q) pi[q] = u[q] >= 0 ? __ldcg(p.pinfo + u[q]) : make_int2(0, 0);
+    // the word of colour t in each target's bitmap; the L1 reads of the
+    // high-degree targets' words (push_bit) are all issued before the atomics
+    const int off = (t - 1) >> 5;
+    const unsigned bit = 1u << ((t - 1) & 31);
+    unsigned seen[kGather];
 #pragma unroll
     for (int q = 0; q < kGather; ++q)
-      if (pi[q].y > 0) push_to(p, pi[q].x, pi[q].y, t);
+      seen[q] = pi[q].y > kDefaultChunk && pi[q].y >= t ? __ldca(p.pbits + pi[q].x + off) : 0u;
+#pragma unroll
+    for (int q = 0; q < kGather; ++q)
+      if (pi[q].y >= t && (seen[q] & bit) == 0) atomicOr(p.pbits + pi[q].x + off, bit);
     return;
   }
   int sw[kGather], ew[kGather], cw[kGather];
