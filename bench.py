@@ -128,6 +128,9 @@ def serving_leg(args, ctx, dev, stream):
         so = server.options(hbm_budget=24 << 30, host_budget=2 << 30, inflight=2,
                             max_batch_graphs=1024)
         so.batch.base.forbidden = ipgc.FORBIDDEN[args.forbidden]
+        # teams of at most 64 CTAs: a large request leaves the rest of its
+        # slot to the small ones (same-GPU sweep of slots and team caps)
+        so.batch.max_team = 64
         srv = server.Server(dev.index or 0, so)
         lat = []
         done_n = [0]
@@ -200,7 +203,7 @@ def serving_leg(args, ctx, dev, stream):
     return {
         "workload": "Poisson arrivals per rate; graphs drawn from 512 graphs shaped like the batched "
                     "workload (seed 5) and, for 1 % of requests, 4 RMAT scale-20 edge-factor-16 graphs",
-        "server": "2 slots, default teams (up to a whole slot), 24 GiB device arena, forbidden "
+        "server": "2 slots, teams of at most 64 CTAs, 24 GiB device arena, forbidden "
                   "colours: " + ("rows rescanned" if args.forbidden == "rescan" else "bitmaps"),
         "seconds_per_rate": args.serve_seconds,
         "rates": out_rates,
