@@ -19,6 +19,9 @@
 #include <vector>
 
 #include "ipgc_internal.h"
+// the batched kernels read the barrier generation at each barrier (see
+// IPGC_BAR_MEMO in ipgc_phases.cuh)
+#define IPGC_BAR_MEMO 0
 #include "ipgc_phases.cuh"
 
 namespace ipgc {

@@ -29,7 +29,7 @@ constexpr int kFiltMaxC = 32 * kGWords - 2;  // neighbour filtering while maxc <
 constexpr int kDefaultFiltDeg = 1024;
 constexpr double kDefaultFiltStart = 1.0 / 32;  // hand over once |WL| <= n / 32
 constexpr int kBarGroups = 16;   // grid barrier: CTAs arrive in this many groups
-constexpr int kBarFlat = 64;     // ... when the team has more CTAs than this
+constexpr int kBarFlat = 128;    // ... when the team has more CTAs than this
 constexpr int kShrinkMin = 8;    // a shrinking team keeps at least this many CTAs
 constexpr int kShrinkMinPush = 64;  // ... with pushing
 constexpr int kStageSmall = 128; // per-warp staging of low-degree pushes
@@ -315,6 +315,14 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* a) {
 // so every CTA leaves its barrier (the count lives in the low 31 bits).
 constexpr uint32_t kBarErr = 0x80000000u;
 
+// What a CTA remembers of its team's barrier (kept in shared memory): the
+// generation the last barrier it passed on control block `ctrl` released
+// (ctrl == nullptr: nothing yet).
+struct BarMemo {
+  const Ctrl* ctrl;
+  uint32_t gen;
+};
+
 // Records an error of the colouring (the first one wins) and raises the
 // barrier's error bit, so that CTAs waiting in a barrier leave it at once.
 __device__ __forceinline__ void record_error(Ctrl* c, int code) {
@@ -331,20 +339,24 @@ __device__ __forceinline__ void record_error(Ctrl* c, int code) {
 // one counter serialise, so 16 short chains and one of 16 beat one of
 // hundreds). `extra` phantom CTAs never arrive (tests).
 //
-// Thread 0 reads the generation before the CTA's warps meet (the barrier
-// cannot complete before this CTA arrives, and this thread has seen the
-// previous one complete, so the value is the current generation); arrivals
-// are acquire-release atomics and the last arrival releases the next
-// generation with an atomic add, which waiters acquire: no separate fences
-// and no further read after the wait.
+// Thread 0 takes the current generation before the CTA's warps meet (the
+// barrier cannot complete before this CTA arrives, and this thread has seen
+// the previous one complete): from `memo`, the generation it saw the
+// previous barrier of the same control block release, or else by reading
+// it. Only the error bit can change the word between two barriers, and a
+// waiter that finds it set leaves with false either way. Arrivals are
+// acquire-release atomics and the last arrival releases the next generation
+// with an atomic add, which waiters acquire: no separate fences and no
+// further read after the wait.
 __device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_t timeout_ns,
-                                             uint32_t extra = 0) {
+                                             uint32_t extra = 0, BarMemo* memo = nullptr) {
   __shared__ int s_ok;
   uint32_t gen = 0;
-  if (threadIdx.x == 0) gen = ld_relaxed_u32(&c->bar_gen);
+  if (threadIdx.x == 0) gen = memo && memo->ctrl == c ? memo->gen : ld_relaxed_u32(&c->bar_gen);
   __syncthreads();
   if (threadIdx.x == 0) {
     bool ok = (gen & kBarErr) == 0;
+    uint32_t next = gen;  // the generation this barrier releases
     if (ok) {
       bool last;
       if (ncta > kBarFlat) {
@@ -362,13 +374,16 @@ __device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_
       }
       if (last) {
         c->bar_count = 0;  // ordered before the release below
-        ok = (atom_add_acq_rel(&c->bar_gen, 1u) & kBarErr) == 0;
+        const uint32_t old = atom_add_acq_rel(&c->bar_gen, 1u);
+        ok = (old & kBarErr) == 0;
+        next = old + 1u;
       } else {
         const uint64_t t0 = gtime();
         while (true) {
           const uint32_t now = ld_acquire_u32(&c->bar_gen);
           if (now != gen) {
             ok = (now & kBarErr) == 0;
+            next = now;
             break;
           }
           if (gtime() - t0 > timeout_ns) {
@@ -379,6 +394,10 @@ __device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_
           __nanosleep(64);
         }
       }
+    }
+    if (memo) {  // a failed barrier is the team's last: forget the control block
+      memo->ctrl = ok ? c : nullptr;
+      memo->gen = next;
     }
     s_ok = ok;
   }

@@ -35,7 +35,22 @@ struct Smem {
   unsigned red3[W];
   unsigned red4[W];
   int rvb[24];  // round state read from the control block once per CTA
+  BarMemo bar;  // the last team barrier this CTA passed (team_barrier)
 };
+
+// Whether team barriers take the generation from the CTA's memo (BarMemo)
+// instead of reading it: on in the single-graph kernels; the batched
+// kernels' translation unit turns it off (there the memo cost registers and
+// 1.2 % of the 4,096-graph batch's time, same GPU, while the single-graph
+// colourings gained 0.5-1.5 %).
+#ifndef IPGC_BAR_MEMO
+#define IPGC_BAR_MEMO 1
+#endif
+
+template <int BS>
+__device__ __forceinline__ BarMemo* bar_memo(Smem<BS>& sm) {
+  return IPGC_BAR_MEMO ? &sm.bar : nullptr;
+}
 
 template <int BS>
 __device__ __forceinline__ void smem_clear(Smem<BS>& sm) {
@@ -43,6 +58,7 @@ __device__ __forceinline__ void smem_clear(Smem<BS>& sm) {
   for (int i = threadIdx.x; i < Smem<BS>::W * 32 * kSmallWords; i += BS) w[i] = 0;
   w = &sm.wbits[0][0];
   for (int i = threadIdx.x; i < Smem<BS>::W * kGWords; i += BS) w[i] = 0;
+  if (threadIdx.x == 0) sm.bar.ctrl = nullptr;
   __syncthreads();
 }
 
@@ -1985,7 +2001,7 @@ __device__ bool team_max_degree(const Params& p, Smem<BS>& sm, Team tm, bool zer
     big = block_sum64<BS>(sm, big);
     if (threadIdx.x == 0 && big) atomicAdd(&p.ctrl->bigsum, big);
   }
-  return team_barrier(p.ctrl, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
+  return team_barrier(p.ctrl, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm));
 }
 
 // Rounds r_start, r_start + 1, ... of one graph by a team of CTAs, separated
@@ -2022,7 +2038,7 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
     if (p.wl_rebuild && rv.mode == MODE_DATA &&
         (r == 2 || ld_cg(&c->mode_at[(r - 1) & 1]) == MODE_TOPO)) {
       rebuild_worklists<BS>(p, sm, rv, tm);
-      if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+      if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm))) break;
       rv.nsmall = ld_cg(&c->rbcnt[0]);
       rv.icnt = ld_cg(&c->rbcnt[1]);
     }
@@ -2045,14 +2061,14 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
     }
     round_begin(p, rv, r, total, tm);
     assign_phase<BS, FILT, PUSH>(p, sm, rv, tm);
-    if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+    if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm))) break;
     if (lead && p.trace && r <= p.trace_cap) p.trace[r - 1].t_assign = gtime();
     {
       PhaseAcc acc;
       detect_phase<BS, FILT, PUSH>(p, sm, rv, acc, tm);
       phase_commit<BS>(p, sm, acc, rv.par ^ 1);
     }
-    if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+    if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm))) break;
     if (PUSH && rv.push) {
       __syncthreads();  // the previous readers of the slots are done
       if (threadIdx.x == 0) {
@@ -2064,7 +2080,7 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       if (q > 0 || w > 0) {
         const uint64_t tp = lead && p.trace && r <= p.trace_cap ? gtime() : 0;
         push_phase<BS>(p, q, w, rv.t1, tm);
-        if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) break;
+        if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm))) break;
         if (tp) p.trace[r - 1].push_ns = (int32_t)(gtime() - tp);
       }
     }
@@ -2114,12 +2130,12 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
     round1<BS, PUSH>(p, sm, acc, tm, t1, pushing);
     phase_commit<BS>(p, sm, acc, 0);
   }
-  bool ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
+  bool ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm));
   if (PUSH && ok && pushing) {
     const int q = read_shared_word<BS>(&c->pqcnt, sm);
     if (q > 0) {
       push_phase<BS>(p, q, 0, t1, tm);
-      ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra);
+      ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm));
     }
   }
   if (ok) {
@@ -2146,7 +2162,7 @@ __device__ void continue_graph(const Params& p, Smem<BS>& sm, Team tm) {
     p.fst[i] = 0;
     p.fdead[i] = 0;
   }
-  if (team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra)) run_rounds<BS, true>(p, sm, tm, r0);
+  if (team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm))) run_rounds<BS, true>(p, sm, tm, r0);
   if (lead) c->t_end = gtime();
 }
 
