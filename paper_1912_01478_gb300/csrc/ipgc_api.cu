@@ -125,7 +125,7 @@ int cuda_fail(ipgc_ctx* ctx, cudaError_t e) {
 //   [n] int2.
 struct WsLayout {
   size_t a4n, items_bytes, gbits_bytes, gint_bytes, alist_bytes, flen_bytes, fst_bytes, pbits_bytes,
-      pq_bytes, pinfo_bytes, total;
+      pq_bytes, pinfo_bytes, rq_bytes, total;
 };
 
 using ipgc::effective_chunk;
@@ -170,10 +170,13 @@ WsLayout ws_layout(int32_t n, int64_t nnz, int t1, int chunk, int filt_deg, bool
   // (ceil(d / kPushChunk) + 1 at most for a row of d entries)
   L.pq_bytes = push ? align256((size_t)(nnz / ipgc::kPushChunk + 2 * nbig + 1) * sizeof(int4)) : 0;
   L.pinfo_bytes = push ? align256((size_t)n * sizeof(int2)) : 0;
+  // list rewrite units of one round: one-window units of the lists of nodes
+  // with a merge-state slot (ceil(L / kPushChunk) + 1 at most for L entries)
+  L.rq_bytes = push ? align256((size_t)(nnz / ipgc::kPushChunk + 2 * gcap + 1) * sizeof(int4)) : 0;
   L.total = 3 * L.a4n + 3 * L.items_bytes + L.gbits_bytes + 3 * L.gint_bytes +
             2 * L.alist_bytes + 2 * L.flen_bytes + 2 * L.fst_bytes +
             (filt ? 2 * L.items_bytes : 0) +
-            (push ? L.pbits_bytes + L.pq_bytes + L.a4n + L.pinfo_bytes : 0);
+            (push ? L.pbits_bytes + L.pq_bytes + L.a4n + L.pinfo_bytes + L.rq_bytes : 0);
   return L;
 }
 
@@ -274,6 +277,8 @@ void fill_params(ipgc_ctx* ctx, Params& p, const int32_t* rowptr, const int32_t*
     p.pw = (int32_t*)w;
     w += L.a4n;
     p.pinfo = (int2*)w;
+    w += L.pinfo_bytes;
+    p.rq = (int4*)w;
   }
   p.ctrl = ctx->d_ctrl;
   p.trace = o.trace;

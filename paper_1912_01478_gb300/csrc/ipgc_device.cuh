@@ -79,6 +79,7 @@ struct Ctrl {
   unsigned long long bigsum;       // entries in the rows of degree > t1 (pushing kernel)
   int32_t pqcnt;                   // push items queued by the current conflict step
   int32_t pwcnt;                   // winners of the current conflict step still to push
+  int32_t rqcnt;                   // list rewrite units queued by the current conflict step
   int32_t push_off;                // the pushing kernel found no node of degree > t1 and left
                                    // the colouring to the rescanning kernel launched after it
   int32_t late_at[2];              // pushing: the latest round of each parity ran late (no push
@@ -164,6 +165,12 @@ struct Params {
   uint32_t* pbits;
   int4* pq;
   int32_t* pw;
+  // With pushing, optional: a loser of a conflict step that is not late and
+  // whose list is due for a rewrite queues it here, in one-window units
+  // {row start, slot, window, list buffer | length << 1}, and the push phase
+  // that follows rewrites it, spread over the whole team (nullptr: the node's
+  // own warps rewrite it in the next assignment step).
+  int4* rq;
   // With pushing, optional: per node {row start, degree} while the node keeps
   // a bitmap and is active, {row start, 0} otherwise (written by round 1, the
   // degree cleared when the node is committed), so a push after round 1

@@ -944,6 +944,20 @@ __device__ __forceinline__ void item_assign_plist(const Params& p, int v, int s,
   }
 }
 
+// The one-window units {row start, slot, length, window | buffer << 31} of
+// the rewrite of list buffer nb (L entries from s) of the node with slot
+// gslot, queued for the push phase. One warp (out of line: it runs rarely).
+inline __device__ __noinline__ void queue_rewrite(const Params& p, int s, int gslot, int L,
+                                                  int nb) {
+  const int lane = lane_id();
+  const int n = push_items_of(s, L);
+  int base = 0;
+  if (lane == 0) base = atomicAdd(&p.ctrl->rqcnt, n);
+  base = __shfl_sync(FULL, base, 0);
+  for (int j = lane; j < n; j += 32)
+    p.rq[base + j] = make_int4(s, gslot, L, (int)((unsigned)j | ((unsigned)nb << 31)));
+}
+
 // Conflict step for work item c of nch of node v with a merge-state slot:
 // its share of the list up to the first clash. The warp that finishes v's
 // last item commits v (queueing its row for the push phase) or pushes its
@@ -1001,7 +1015,7 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
   hit = __any_sync(FULL, hit);
   dead = __reduce_add_sync(FULL, dead);
   seen = __reduce_add_sync(FULL, seen);
-  int finisher = 0, lose = 0;
+  int finisher = 0, lose = 0, requeue = 0;
   if (lane == 0) {
     int D = dead, S = seen;
     if (nch == 1) {  // the only item: nothing to merge
@@ -1024,11 +1038,24 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
     if (finisher) {
       const bool rw = D > 0 && 4 * (int64_t)D >= (int64_t)S;
       if ((st & 6) == 6) p.flen[cur][gslot] = make_int2(0, 0);  // rewritten: the old buffer is free
-      p.fst[gslot] = nb | 4 | (rw ? 2 : 0);
+      // a loser due for a rewrite in a round with a push phase: that phase
+      // rewrites the list into the other buffer, which round r + 1 reads
+      // (in a late round, or without a queue, its next assignment step does).
+      // Both lengths start again from zero: the units carry the old one, and
+      // no item of this node reads it any more (this is its last item of the
+      // round, and round r + 1 reads the other buffer), so the old buffer is
+      // empty when a later rewrite appends to it.
+      requeue = rw && lose && p.rq != nullptr && !late && lists_next;
+      if (requeue) {
+        p.flen[nb ^ 1][gslot] = make_int2(0, 0);
+        p.flen[nb][gslot] = make_int2(0, 0);
+      }
+      p.fst[gslot] = requeue ? ((nb ^ 1) | 4) : (nb | 4 | (rw ? 2 : 0));
     }
   }
   finisher = __shfl_sync(FULL, finisher, 0);
   lose = __shfl_sync(FULL, lose, 0);
+  if (__shfl_sync(FULL, requeue, 0)) queue_rewrite(p, s, gslot, L, nb);
   const int nxt_items = lists_next ? max(1, num_chunks(L, p.chunk)) : num_chunks(d, p.chunk);
   items_push(stage, v, (push && finisher && lose && lane == 0) ? nxt_items : 0, gslot,
              p.items[nxt], &p.ctrl->icnt[nxt]);
@@ -1512,6 +1539,7 @@ __device__ __forceinline__ void round_begin(const Params& p, const RoundView& rv
   c->dsum[nxt] = 0;
   c->pqcnt = 0;
   c->pwcnt = 0;
+  c->rqcnt = 0;
   c->late_at[r & 1] = rv.late ? 1 : 0;
   c->rounds = r;
   c->maxc_start[r & 1] = rv.maxc;
@@ -1826,10 +1854,12 @@ __device__ void detect_phase(const Params& p, Smem<BS>& sm, const RoundView& rv,
 // degree > t1 (one warp each; a warp loads its next item's window and the
 // record after that before it pushes the current one, so their latency
 // overlaps the pushes' gathers), then the listed low-degree winners 32 at a
-// time (their rows laid end to end, at most 32 * t1 entries). A team
-// barrier follows.
+// time (their rows laid end to end, at most 32 * t1 entries), then the
+// one-window units of the list rewrites the conflict step queued (the
+// entries still active after it, appended to the node's other list buffer).
+// A team barrier follows.
 template <int BS>
-__device__ __noinline__ void push_phase(const Params& p, int nq, int nw, int t1, Team tm) {
+__device__ __noinline__ void push_phase(const Params& p, int nq, int nw, int nr, int t1, Team tm) {
   const int gwarp = tm.cta * (BS / 32) + (threadIdx.x >> 5), nwarps = tm.ncta * (BS / 32);
   const int lane = lane_id();
   const int units = nq + (nw + 31) / 32;
@@ -1880,6 +1910,13 @@ __device__ __noinline__ void push_phase(const Params& p, int nq, int nw, int t1,
       d = dn;
       t = tn;
     }
+  }
+  for (; k < units + nr; k += nwarps) {  // list rewrites {row start, slot, length, window | buffer}
+    const int4 it = ld_cg4(p.rq + (k - units));
+    const int src = (int)((unsigned)it.w >> 31), j = it.w & 0x7fffffff;
+    const int64_t s = it.x, a = (s & ~int64_t(3)) + (int64_t)j * kPushChunk;
+    plist_append(p, p.alist[src], false, a > s ? a : s, min(s + it.z, a + kPushChunk), INT_MAX, s,
+                 p.alist[src ^ 1], &p.flen[src ^ 1][it.y].x);
   }
 }
 
@@ -2074,12 +2111,13 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
       if (threadIdx.x == 0) {
         sm.rvb[20] = ld_cg(&c->pqcnt);
         sm.rvb[21] = ld_cg(&c->pwcnt);
+        sm.rvb[22] = ld_cg(&c->rqcnt);
       }
       __syncthreads();
-      const int q = sm.rvb[20], w = sm.rvb[21];
-      if (q > 0 || w > 0) {
+      const int q = sm.rvb[20], w = sm.rvb[21], nr = sm.rvb[22];
+      if (q > 0 || w > 0 || nr > 0) {
         const uint64_t tp = lead && p.trace && r <= p.trace_cap ? gtime() : 0;
-        push_phase<BS>(p, q, w, rv.t1, tm);
+        push_phase<BS>(p, q, w, nr, rv.t1, tm);
         if (!team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm))) break;
         if (tp) p.trace[r - 1].push_ns = (int32_t)(gtime() - tp);
       }
@@ -2134,7 +2172,7 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   if (PUSH && ok && pushing) {
     const int q = read_shared_word<BS>(&c->pqcnt, sm);
     if (q > 0) {
-      push_phase<BS>(p, q, 0, t1, tm);
+      push_phase<BS>(p, q, 0, 0, t1, tm);
       ok = team_barrier(c, tm.cta, tm.ncta, p.timeout_ns, p.bar_extra, bar_memo<BS>(sm));
     }
   }
