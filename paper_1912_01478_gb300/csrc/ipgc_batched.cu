@@ -361,8 +361,8 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
 
   // per-graph slices of the workspace
   std::vector<int64_t> item_base(num_graphs + 1), gbase(num_graphs + 1), pq_base(num_graphs + 1),
-      lbase(num_graphs + 1);
-  item_base[0] = gbase[0] = pq_base[0] = lbase[0] = 0;
+      lbase(num_graphs + 1), rq_base(num_graphs + 1);
+  item_base[0] = gbase[0] = pq_base[0] = lbase[0] = rq_base[0] = 0;
   for (int32_t g = 0; g < num_graphs; ++g) {
     const int64_t n = node_off[g + 1] - node_off[g], e = edge_off[g + 1] - edge_off[g];
     int64_t nbig = e / (t1 + 1);
@@ -370,6 +370,8 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
     item_base[g + 1] = item_base[g] + e / chunk + nbig + 1;
     gbase[g + 1] = gbase[g] + e / ((int64_t)chunk + 1) + 1;
     pq_base[g + 1] = pq_base[g] + (push ? e / ipgc::kPushChunk + 2 * nbig + 1 : 0);
+    // list rewrite units (one window each) of the graph's merge-state slots
+    rq_base[g + 1] = rq_base[g] + (push ? e / ipgc::kPushChunk + 2 * (gbase[g + 1] - gbase[g]) + 1 : 0);
     // lists are read as int4 windows from their buffer's base: every graph's
     // slice starts on a 16-byte boundary
     lbase[g + 1] = lbase[g] + (push ? (e + 3) / 4 * 4 : 0);
@@ -412,9 +414,10 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   const size_t b_pw = push ? b_node : 0;
   // ... and per node {row start, degree while active and bitmapped} (push targets)
   const size_t b_pinfo = push ? al256(sizeof(int2) * (size_t)total_n) : 0;
+  const size_t b_rq = al256(sizeof(int4) * (size_t)rq_base[num_graphs]);
   const size_t need = b_params + b_lists + b_plists + b_ctrl + 3 * b_node + 3 * b_items + b_gbits +
                       3 * b_gint + b_edge + 2 * b_lists_e + 2 * b_gint2 + 2 * b_gpint + b_pq +
-                      b_pw + b_pinfo + 256;
+                      b_pw + b_pinfo + b_rq + 256;
   if (W->dev_bytes < need || W->device != dev) {
     if (W->dev) cudaFree(W->dev);
     W->dev = nullptr;
@@ -480,6 +483,8 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
   w += b_pw;
   int2* d_pinfo = (int2*)w;
   w += b_pinfo;
+  int4* d_rq = (int4*)w;
+  w += b_rq;
   ipgc::ValidateState* d_err = (ipgc::ValidateState*)w;
 
   // optional validation of every graph (one launch per graph)
@@ -540,6 +545,7 @@ int ipgc_color_batched(ipgc_ctx* ctx, int32_t num_graphs, const int64_t* node_of
       p.pq = d_pq + pq_base[g];
       p.pw = d_pw + node_off[g];
       p.pinfo = d_pinfo + node_off[g];
+      p.rq = d_rq + rq_base[g];
     }
   }
 

@@ -134,11 +134,12 @@ struct Slot {
 
 // Per-request device layout (offsets from the request's block); with
 // pushing also the bitmaps, the two list buffers, the list counts and state,
-// the push queue, the winners and the push targets (offsets 0 without).
+// the push queue, the winners, the push targets and the list rewrite queue
+// (offsets 0 without).
 struct DevLayout {
   size_t rowptr, col, colors, tent, wl0, wl1, it0, it1, its, gbits, done_a, done_d, flag;
   size_t pbits = 0, alist0 = 0, alist1 = 0, flen0 = 0, flen1 = 0, fst = 0, fdead = 0, pq = 0,
-         pw = 0, pinfo = 0;
+         pw = 0, pinfo = 0, rq = 0;
   size_t total;
   int64_t icap, gcap;
 };
@@ -180,6 +181,7 @@ DevLayout dev_layout(int32_t n, int64_t nnz, int t1, int chunk, bool push) {
     L.pq = take(16 * (size_t)(nnz / ipgc::kPushChunk + 2 * nbig + 1));
     L.pw = take(4 * (size_t)n);
     L.pinfo = take(8 * (size_t)n);
+    L.rq = take(16 * (size_t)(nnz / ipgc::kPushChunk + 2 * L.gcap + 1));
   }
   L.total = o;
   return L;
@@ -390,6 +392,7 @@ bool launch_locked(ipgc_server* S) {
       p.pq = (int4*)(b + L.pq);
       p.pw = (int32_t*)(b + L.pw);
       p.pinfo = (int2*)(b + L.pinfo);
+      p.rq = (int4*)(b + L.rq);
     }
   }
   int rc = IPGC_OK;
