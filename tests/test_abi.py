@@ -134,8 +134,10 @@ def test_workspace_size_by_forbidden_colour_source(lib):
     assert push < auto <= push + 2 * items + 512
     assert size(driver="hostloop") == rescan
     assert rescan - plain >= 8 * nnz
-    # + bitmaps (4 nnz) + winners (4 n) + queue, - the filtered items (2 x 16 B per item)
-    assert 3.5 * nnz < push - rescan < 4 * nnz + 4 * n + 16 * (nnz // 128 + n + 1)
+    # + bitmaps (4 nnz) + winners (4 n) + push targets (8 n) + the push and list
+    # rewrite queues (16 B per 128 entries each, plus per node), - the filtered
+    # items (2 x 16 B per item)
+    assert 3.5 * nnz < push - rescan < 4 * nnz + 12 * n + 32 * (nnz // 128 + n + 1)
 
 
 def test_host_validation(lib):
