@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_kernel(const __
   // after a pushing kernel (p.pbits set) only when that one left the colouring to this one
   if (p.pbits && ld_cg(&p.ctrl->push_off) == 0) return;
   __shared__ Smem<BS> sm;
-  smem_clear<BS>(sm);
+  smem_clear<BS>(sm, 1);
   color_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
 }
 
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(BS, push_min_blocks(BS)) persistent_push_kerne
 template <int BS>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) persistent_filt_kernel(const __grid_constant__ Params p) {
   __shared__ Smem<BS> sm;
-  smem_clear<BS>(sm);
+  smem_clear<BS>(sm, 2);
   continue_graph<BS>(p, sm, Team{(int)blockIdx.x, (int)gridDim.x});
 }
 

@@ -88,6 +88,10 @@ struct Ctrl {
   int32_t push_on;                 // forbidden-colour bitmaps in use (some degree > t1)
   // arrival counters of the grid barrier's groups, one 32-byte sector each
   uint32_t bar_grp[kBarGroups][8];
+  // arrival counts of the counting barrier (team_barrier with a memo), one
+  // per single-graph kernel of a colouring (pushing, rescanning, filtering),
+  // each starting from zero with the control block; bit 63: error
+  unsigned long long bar_arrive[3];
 };
 
 struct Params {
@@ -312,6 +316,14 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* a) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
   return v;
 }
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* a, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* a) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+  return v;
+}
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* a) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
@@ -327,7 +339,8 @@ constexpr uint32_t kBarErr = 0x80000000u;
 // (ctrl == nullptr: nothing yet).
 struct BarMemo {
   const Ctrl* ctrl;
-  uint32_t gen;
+  int idx;                     // the kernel's arrival counter (Ctrl::bar_arrive)
+  unsigned long long target;   // arrivals at which that barrier completed
 };
 
 // Records an error of the colouring (the first one wins) and raises the
@@ -335,6 +348,8 @@ struct BarMemo {
 __device__ __forceinline__ void record_error(Ctrl* c, int code) {
   atomicCAS(&c->status, 0, code);
   atomicOr(&c->bar_gen, kBarErr);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) atomicOr(&c->bar_arrive[k], 1ull << 63);
 }
 
 // Barrier of a team of co-resident CTAs (a cooperative launch guarantees
@@ -349,24 +364,61 @@ __device__ __forceinline__ void record_error(Ctrl* c, int code) {
 // faster flat than in 16 groups, same GPU). `extra` phantom CTAs never arrive
 // (tests).
 //
-// Thread 0 takes the current generation before the CTA's warps meet (the
-// barrier cannot complete before this CTA arrives, and this thread has seen
-// the previous one complete): from `memo`, the generation it saw the
-// previous barrier of the same control block release, or else by reading
-// it. Only the error bit can change the word between two barriers, and a
-// waiter that finds it set leaves with false either way. Arrivals are
-// acquire-release atomics and the last arrival releases the next generation
-// with an atomic add, which waiters acquire: no separate fences and no
-// further read after the wait.
+// Thread 0 reads the generation before the CTA's warps meet (the barrier
+// cannot complete before this CTA arrives, and this thread has seen the
+// previous one complete, so the value is the current generation); arrivals
+// are acquire-release atomics and the last arrival releases the next
+// generation with an atomic add, which waiters acquire: no separate fences
+// and no further read after the wait.
+//
+// With a memo (the single-graph kernels) the barrier counts instead: each
+// CTA adds its arrival to the kernel's 64-bit arrival count with a release
+// reduction (no reply to wait for) and waits, acquiring, until the count
+// reaches the barrier's target, which the CTA keeps in its memo: the previous
+// barrier's target plus the team's size (the count starts at zero with the
+// control block, every barrier of the team adds exactly its size, and a team
+// that shrinks does so between barriers, the same for every CTA). No CTA
+// waits on a reply to its arrival and no generation is released: one
+// dependent round trip fewer than the generation barrier. An error sets bit
+// 63 of the count, and a waiter that sees it leaves with false.
 __device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_t timeout_ns,
                                              uint32_t extra = 0, BarMemo* memo = nullptr) {
   __shared__ int s_ok;
+  if (memo) {  // the counting barrier
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long* w = &c->bar_arrive[memo->idx];
+      const unsigned long long target =
+          (memo->ctrl == c ? memo->target : 0ull) + (unsigned long long)ncta + extra;
+      red_release_add_u64(w, 1ull);
+      bool ok = true;
+      const uint64_t t0 = gtime();
+      while (true) {
+        const unsigned long long now = ld_acquire_u64(w);
+        if (now >> 63) {
+          ok = false;
+          break;
+        }
+        if (now >= target) break;
+        if (gtime() - t0 > timeout_ns) {
+          record_error(c, IPGC_ERR_TIMEOUT);
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+      memo->ctrl = ok ? c : nullptr;  // a failed barrier is the team's last
+      memo->target = target;
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
   uint32_t gen = 0;
-  if (threadIdx.x == 0) gen = memo && memo->ctrl == c ? memo->gen : ld_relaxed_u32(&c->bar_gen);
+  if (threadIdx.x == 0) gen = ld_relaxed_u32(&c->bar_gen);
   __syncthreads();
   if (threadIdx.x == 0) {
     bool ok = (gen & kBarErr) == 0;
-    uint32_t next = gen;  // the generation this barrier releases
     if (ok) {
       bool last;
       if (ncta > kBarFlat) {
@@ -384,16 +436,13 @@ __device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_
       }
       if (last) {
         c->bar_count = 0;  // ordered before the release below
-        const uint32_t old = atom_add_acq_rel(&c->bar_gen, 1u);
-        ok = (old & kBarErr) == 0;
-        next = old + 1u;
+        ok = (atom_add_acq_rel(&c->bar_gen, 1u) & kBarErr) == 0;
       } else {
         const uint64_t t0 = gtime();
         while (true) {
           const uint32_t now = ld_acquire_u32(&c->bar_gen);
           if (now != gen) {
             ok = (now & kBarErr) == 0;
-            next = now;
             break;
           }
           if (gtime() - t0 > timeout_ns) {
@@ -404,10 +453,6 @@ __device__ __forceinline__ bool team_barrier(Ctrl* c, int cta, int ncta, uint64_
           __nanosleep(64);
         }
       }
-    }
-    if (memo) {  // a failed barrier is the team's last: forget the control block
-      memo->ctrl = ok ? c : nullptr;
-      memo->gen = next;
     }
     s_ok = ok;
   }

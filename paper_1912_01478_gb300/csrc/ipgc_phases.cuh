@@ -38,11 +38,10 @@ struct Smem {
   BarMemo bar;  // the last team barrier this CTA passed (team_barrier)
 };
 
-// Whether team barriers take the generation from the CTA's memo (BarMemo)
-// instead of reading it: on in the single-graph kernels; the batched
-// kernels' translation unit turns it off (there the memo cost registers and
-// 1.2 % of the 4,096-graph batch's time, same GPU, while the single-graph
-// colourings gained 0.5-1.5 %).
+// Whether team barriers count arrivals against the CTA's memo (BarMemo)
+// instead of releasing generations: on in the single-graph kernels; the
+// batched kernels' translation unit turns it off (a memo there cost
+// registers and 1.2 % of the 4,096-graph batch's time, same GPU).
 #ifndef IPGC_BAR_MEMO
 #define IPGC_BAR_MEMO 1
 #endif
@@ -52,13 +51,18 @@ __device__ __forceinline__ BarMemo* bar_memo(Smem<BS>& sm) {
   return IPGC_BAR_MEMO ? &sm.bar : nullptr;
 }
 
+// bar_idx: the kernel's arrival counter for the counting barrier (one per
+// single-graph kernel of a colouring: 0 pushing, 1 rescanning, 2 filtering).
 template <int BS>
-__device__ __forceinline__ void smem_clear(Smem<BS>& sm) {
+__device__ __forceinline__ void smem_clear(Smem<BS>& sm, int bar_idx = 0) {
   unsigned* w = &sm.small_w[0][0];
   for (int i = threadIdx.x; i < Smem<BS>::W * 32 * kSmallWords; i += BS) w[i] = 0;
   w = &sm.wbits[0][0];
   for (int i = threadIdx.x; i < Smem<BS>::W * kGWords; i += BS) w[i] = 0;
-  if (threadIdx.x == 0) sm.bar.ctrl = nullptr;
+  if (threadIdx.x == 0) {
+    sm.bar.ctrl = nullptr;
+    sm.bar.idx = bar_idx;
+  }
   __syncthreads();
 }
 
