@@ -19,9 +19,6 @@
 #include <vector>
 
 #include "ipgc_internal.h"
-// the batched kernels read the barrier generation at each barrier (see
-// IPGC_BAR_MEMO in ipgc_phases.cuh)
-#define IPGC_BAR_MEMO 0
 #include "ipgc_phases.cuh"
 
 namespace ipgc {
@@ -74,7 +71,7 @@ template <int BS>
 __global__ void __launch_bounds__(BS, min_blocks(BS)) batched_kernel(BatchParams bp) {
   __shared__ Smem<BS> sm;
   __shared__ int s_k;
-  smem_clear<BS>(sm);
+  smem_clear<BS>(sm, 1);  // (the pushing batched kernel counts on counter 0)
   batched_jobs<BS, false>(bp, sm, &s_k);
 }
 

@@ -39,9 +39,8 @@ struct Smem {
 };
 
 // Whether team barriers count arrivals against the CTA's memo (BarMemo)
-// instead of releasing generations: on in the single-graph kernels; the
-// batched kernels' translation unit turns it off (a memo there cost
-// registers and 1.2 % of the 4,096-graph batch's time, same GPU).
+// instead of releasing generations: on in every kernel that colours graphs
+// (a translation unit may turn it off by defining it as 0).
 #ifndef IPGC_BAR_MEMO
 #define IPGC_BAR_MEMO 1
 #endif
