@@ -228,6 +228,27 @@ def test_batch_shapes_single(ctx):
         assert_parity(ctx, rp, cl)
 
 
+def test_finalisation_rounds_when_no_node_keeps_a_bitmap(ctx):
+    # graphs without a node above t1 (a road grid, a mesh): the pushing
+    # kernel hands them to the rescanning kernel after its degree pass; the
+    # per-node finalisation rounds and the trace must still be the oracle's
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc
+
+    for rp, cl in (graphgen.road(300, seed=41), graphgen.lattice3(24, 6)):
+        ref = oracle.color(rp, cl, trace=True)
+        assert int(np.diff(rp).max()) <= 255
+        drp, dcl = to_dev(rp, cl)
+        fin = torch.zeros(rp.size - 1, dtype=torch.int32, device="cuda")
+        tr = ipgc.trace_buffer(ref.rounds + 2)
+        colors, st = ctx.color(drp, dcl, trace=tr, fin_round=fin)
+        assert np.array_equal(colors.cpu().numpy(), ref.colors)
+        assert np.array_equal(fin.cpu().numpy(), ref.fin_round)
+        t = ipgc.read_trace(tr, st.rounds)
+        assert t["wl_size"].tolist() == list(ref.wl_sizes)
+
+
 def test_trace_matches_oracle(ctx):
     import torch
 
