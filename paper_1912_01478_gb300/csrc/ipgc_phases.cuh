@@ -35,6 +35,8 @@ struct Smem {
   unsigned red3[W];
   unsigned red4[W];
   int rvb[24];  // round state read from the control block once per CTA
+  int rvn[16];  // round rvn_round's state, read ahead (before a push phase)
+  int rvn_round;
   BarMemo bar;  // the last team barrier this CTA passed (team_barrier)
 };
 
@@ -61,6 +63,7 @@ __device__ __forceinline__ void smem_clear(Smem<BS>& sm, int bar_idx = 0) {
   if (threadIdx.x == 0) {
     sm.bar.ctrl = nullptr;
     sm.bar.idx = bar_idx;
+    sm.rvn_round = 0;
   }
   __syncthreads();
 }
@@ -1445,18 +1448,28 @@ struct RoundView {
 // per lane) into shared memory and handed to every thread of the CTA: all
 // warps of a large team loading the same few lines at once would queue at
 // one L2 slice after every barrier. Called by every thread of the CTA.
+// The 14 control-block words of round r's state into dst (warp 0). All of
+// them are final once round r - 1's conflict step is over: its push phase
+// writes none of them.
+__device__ __forceinline__ void load_round_words(const Params& p, int r, int* dst) {
+  const int par = r & 1;
+  const Ctrl* c = p.ctrl;
+  const int32_t* dsum = reinterpret_cast<const int32_t*>(&c->dsum[par]);
+  const int32_t* src[14] = {&c->cnt[par][B_SMALL], &c->cnt[par][B_BIG], &c->icnt[par], &c->nistat,
+                            &c->ficnt[par],        &c->t1,             &c->maxc,       dsum,
+                            dsum + 1,              &c->handoff_round,  &c->maxc_start[(r - 1) & 1],
+                            &c->push_on,           &c->cnt[par][2],    &c->late_at[(r - 1) & 1]};
+  const int lane = lane_id();
+  if (lane < 14) dst[lane] = ld_cg(src[lane]);
+}
+
 template <int BS>
 __device__ __forceinline__ RoundView read_round(const Params& p, int r, Smem<BS>& sm) {
   const int par = r & 1;
-  if (threadIdx.x < 32) {
-    const Ctrl* c = p.ctrl;
-    const int32_t* dsum = reinterpret_cast<const int32_t*>(&c->dsum[par]);
-    const int32_t* src[14] = {&c->cnt[par][B_SMALL], &c->cnt[par][B_BIG], &c->icnt[par], &c->nistat,
-                              &c->ficnt[par],        &c->t1,             &c->maxc,       dsum,
-                              dsum + 1,              &c->handoff_round,  &c->maxc_start[(r - 1) & 1],
-                              &c->push_on,           &c->cnt[par][2],    &c->late_at[(r - 1) & 1]};
-    const int lane = lane_id();
-    if (lane < 14) sm.rvb[lane] = ld_cg(src[lane]);
+  if (sm.rvn_round == r) {  // read ahead, before the previous round's push phase
+    if (threadIdx.x < 14) sm.rvb[threadIdx.x] = sm.rvn[threadIdx.x];
+  } else if (threadIdx.x < 32) {
+    load_round_words(p, r, sm.rvb);
   }
   __syncthreads();
   RoundView rv;
@@ -2115,7 +2128,11 @@ __device__ void run_rounds(const Params& p, Smem<BS>& sm, Team tm, int r_start) 
         sm.rvb[20] = ld_cg(&c->pqcnt);
         sm.rvb[21] = ld_cg(&c->pwcnt);
         sm.rvb[22] = ld_cg(&c->rqcnt);
+        sm.rvn_round = r + 1;
       }
+      // the next round's state in the same round trip (final after this
+      // conflict step), so the next round starts without reading it
+      if (threadIdx.x < 32) load_round_words(p, r + 1, sm.rvn);
       __syncthreads();
       const int q = sm.rvb[20], w = sm.rvb[21], nr = sm.rvb[22];
       if (q > 0 || w > 0 || nr > 0) {
@@ -2139,6 +2156,7 @@ __device__ void color_graph(const Params& p, Smem<BS>& sm, Team tm) {
   const bool lead = tm.cta == 0 && threadIdx.x == 0;
   const uint64_t t0 = gtime();
   if (lead && c->t_start == 0) c->t_start = t0;  // (a pushing kernel before this one may have set it)
+  if (threadIdx.x == 0) sm.rvn_round = 0;  // nothing read ahead for this graph yet
   int t1 = p.t1;
   bool pushing = false;
   // a pushing kernel that left the colouring to this one found the largest degree already
@@ -2194,6 +2212,7 @@ __device__ void continue_graph(const Params& p, Smem<BS>& sm, Team tm) {
   Ctrl* c = p.ctrl;
   const int r0 = ld_cg(&c->handoff_round);
   if (r0 == 0) return;
+  if (threadIdx.x == 0) sm.rvn_round = 0;
   const bool lead = tm.cta == 0 && threadIdx.x == 0;
   // list counts of every merge-state slot start at zero
   const int ng = ld_cg(&c->ngslot);
