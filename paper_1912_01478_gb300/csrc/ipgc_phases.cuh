@@ -979,8 +979,11 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
   const uint64_t pol = l2_keep_policy();
   const int t = ld_cg(p.tent + v);
   const int st = ld_cg(p.fst + gslot);
-  // both buffers' lengths together with the state: one round trip, not two
+  // both buffers' lengths and the clash flag together with the state: one
+  // round trip (the flag only for a node of several items: no other item
+  // sets it otherwise)
   const int L0 = ld_cg(&p.flen[0][gslot].x), L1 = ld_cg(&p.flen[1][gslot].x);
+  const int clashed = nch > 1 ? ld_cg(p.flag + gslot) : 0;
   const int cur = st & 1;
   const int nb = !(st & 4) ? 0 : ((st & 2) ? cur ^ 1 : cur);
   const int L = nb ? L1 : L0;
@@ -988,7 +991,7 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
   const int64_t lo = s + (int64_t)L * c / nch, hi = s + (int64_t)L * (c + 1) / nch;
   bool hit = false;
   int dead = 0, seen = 0;
-  if (lo < hi && ld_cg(p.flag + gslot) == 0) {  // else another item found a clash already
+  if (lo < hi && clashed == 0) {  // else another item found a clash already
     int64_t a = lo & ~int64_t(3);
     int u[kGather];
     load_window_rw(lst, a, lo, hi, -1, u);
