@@ -44,6 +44,7 @@ def autotune(ctx: "ipgc.Context", node_off, edge_off, rowptr_cat, col_cat, color
     edge_off = np.ascontiguousarray(edge_off, dtype=np.int64)
     o = opts if opts is not None else options()
     best = ctypes.c_float(0)
+    ipgc._after_current(stream)
     rc = lib().ipgc_batched_autotune(
         ctx.handle, node_off.size - 1, node_off.ctypes.data, edge_off.ctypes.data,
         rowptr_cat.data_ptr(), col_cat.data_ptr(), colors_cat.data_ptr(), sample_graphs, reps,
@@ -125,6 +126,7 @@ def color_batched(ctx: "ipgc.Context", node_off: np.ndarray, edge_off: np.ndarra
     if colors_cat is None:
         colors_cat = torch.empty(max(total_n, 0), dtype=torch.int32, device=rowptr_cat.device)
     st = (ipgc.Stats * max(G, 1))() if want_stats else None
+    ipgc._after_current(stream)
     rc = lib().ipgc_color_batched(
         ctx.handle, G, node_off.ctypes.data, edge_off.ctypes.data, rowptr_cat.data_ptr(),
         col_cat.data_ptr() if col_cat.numel() else None,

@@ -221,6 +221,21 @@ def _stream_handle(stream) -> int:
     return int(stream.cuda_stream)  # torch.cuda.Stream
 
 
+def _after_current(stream) -> None:
+    """Order a torch stream after the work already queued on the current torch
+    stream of its device, where the caller's buffers were allocated, zeroed or
+    copied (a trace buffer or finalisation array zeroed there could otherwise
+    be zeroed again while the colouring writes it). Raw stream handles are the
+    caller's to order."""
+    if stream is None or isinstance(stream, int):
+        return
+    import torch
+
+    cur = torch.cuda.current_stream(stream.device)
+    if cur != stream:
+        stream.wait_stream(cur)
+
+
 def _check(rc: int, what: str):
     if rc != IPGC_OK:
         raise IpgcError(rc, what)
@@ -270,6 +285,7 @@ class Context:
             tptr, tcap = trace.data_ptr(), trace.numel() // ctypes.sizeof(TraceRec)
         o = opts.to_c(tptr, tcap, fin_round.data_ptr() if fin_round is not None else 0)
         st = Stats()
+        _after_current(stream)
         rc = lib().ipgc_color_ex(
             self.handle,
             rowptr.data_ptr(),
@@ -333,6 +349,7 @@ class Context:
 
     def validate(self, rowptr, col, stream=None) -> int:
         """IPGC_OK or IPGC_ERR_INVALID for a CSR held in CUDA tensors."""
+        _after_current(stream)
         return lib().ipgc_validate_csr(
             self.handle, rowptr.data_ptr(), col.data_ptr() if col.numel() else None,
             rowptr.numel() - 1, col.numel(), 1, _stream_handle(stream) or None,

@@ -249,6 +249,29 @@ def test_finalisation_rounds_when_no_node_keeps_a_bitmap(ctx):
         assert t["wl_size"].tolist() == list(ref.wl_sizes)
 
 
+def test_buffers_zeroed_on_the_current_stream_before_a_side_stream_colouring(ctx):
+    # the binding orders a colouring on another torch stream after the work
+    # queued on the current one: a large trace buffer and the finalisation
+    # array are zeroed there just before the call, and the zero fill must not
+    # land on what the colouring writes
+    import torch
+
+    from paper_1912_01478_gb300 import ipgc
+
+    rp, cl = graphgen.road(1000, seed=43)
+    ref = oracle.color(rp, cl, trace=True)
+    drp, dcl = to_dev(rp, cl)
+    side = torch.cuda.Stream()
+    for _ in range(3):
+        tr = ipgc.trace_buffer(rp.size + 1)  # about 56 MB of zero fill first
+        fin = torch.zeros(rp.size - 1, dtype=torch.int32, device="cuda")
+        colors, st = ctx.color(drp, dcl, stream=side, trace=tr, fin_round=fin)
+        assert np.array_equal(colors.cpu().numpy(), ref.colors)
+        assert np.array_equal(fin.cpu().numpy(), ref.fin_round)
+        t = ipgc.read_trace(tr, st.rounds)
+        assert t["wl_size"].tolist() == list(ref.wl_sizes)
+
+
 def test_trace_matches_oracle(ctx):
     import torch
 
