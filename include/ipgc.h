@@ -156,10 +156,10 @@ typedef struct ipgc_options {
                              which each neighbour ORs its colour once, when it is committed, so
                              a row is read about once in all instead of once per round; a node
                              with several work items also keeps the list of its still-active
-                             lower-ID neighbours for its conflict step. Same colours; 12 more
-                             bytes of workspace per entry; needs the persistent driver
-                             (IPGC_ERR_UNSUPPORTED otherwise); forced, it turns neighbour
-                             filtering off;
+                             lower-ID neighbours for its conflict step. Same colours; about 12
+                             more bytes of workspace per entry and 12 per node; needs the
+                             persistent driver (IPGC_ERR_UNSUPPORTED otherwise); forced, it
+                             turns neighbour filtering off;
                              rounds that start with a colour above 2046 committed rescan; a
                              graph without a node of degree > t1 is coloured by rescanning.
                              IPGC_FORBIDDEN_AUTO (0, default): PUSH with the persistent driver

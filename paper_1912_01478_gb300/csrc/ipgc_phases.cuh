@@ -818,9 +818,11 @@ __device__ __forceinline__ void item_detect(const Params& p, ItemStage& stage, i
 // reads the list instead of the lower part of its row: every active
 // lower-ID neighbour is on it, and the finalised ones it may still hold
 // cannot clash (tent[v] excludes their colours). The first assignment step
-// after round 1 builds it from the row; later ones rewrite it, without its
-// finalised entries, once a quarter of the entries the conflict step
-// sampled were finalised.
+// after round 1 builds it from the row. Once a quarter of the entries the
+// conflict step sampled were finalised, the list is rewritten without its
+// finalised entries into the other buffer: by the push phase that follows
+// that conflict step (queue_rewrite, spread over the team), or, after a late
+// round, which has no push phase, by the node's next assignment step.
 
 // Entries [lo, hi) of src (the sorted row when from_col): those of ID < v
 // whose colour is 0 appended to v's list at dst[s + *len...]. One warp.
