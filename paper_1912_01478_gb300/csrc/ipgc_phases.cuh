@@ -970,9 +970,9 @@ inline __device__ __noinline__ void queue_rewrite(const Params& p, int s, int gs
 // its share of the list up to the first clash. The warp that finishes v's
 // last item commits v (queueing its row for the push phase) or pushes its
 // items for round r + 1 (chunks of the list while the next round pushes,
-// else of the row), and sets the list state. The finalised entries among
-// the first window of each item are counted in fdead, all entries of those
-// windows in done_a (idle in this mode).
+// else of the row), and sets the list state. In odd rounds the finalised
+// entries among the first window of each item are counted in fdead, all
+// entries of those windows in done_a (idle in this mode).
 __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& stage, int v, int s,
                                                   int d, int c, int nch, int gslot, int nxt,
                                                   PhaseAcc& acc, int round, bool push,
@@ -1006,7 +1006,10 @@ __device__ __forceinline__ void item_detect_plist(const Params& p, ItemStage& st
       for (int q = 0; q < kGather; ++q) tt[q] = u[q] >= 0 ? ld_keep(p.tent + u[q], pol) : 0;
 #pragma unroll
       for (int q = 0; q < kGather; ++q) hit |= u[q] >= 0 && tt[q] == t;
-      if (a < lo + kWindow) {  // the item's first window samples how much of the list is finalised
+      // in odd rounds the item's first window samples how much of the list is
+      // finalised (each sample is a second gather per entry; every other
+      // round is often enough for the rewrites it triggers)
+      if ((round & 1) && a < lo + kWindow) {
         int cc[kGather];
 #pragma unroll
         for (int q = 0; q < kGather; ++q) cc[q] = u[q] >= 0 ? ld_keep(p.color + u[q], pol) : 0;
